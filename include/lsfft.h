@@ -1,0 +1,149 @@
+/*
+ * lsfft.h - C ABI of the GB300 (sm_103a) FFT Lippmann-Schwinger solver for
+ * two-phase periodic conductors.
+ *
+ * Method: G. W. Milton, "Substitution of subspace collections with
+ * nonorthogonal subspaces to accelerate Fast Fourier Transform methods applied
+ * to conducting composites" (arXiv 2001.08289).
+ *
+ *   Problem (Eq. J12, J13): sigma(x) = 1 + (sigma_1 - 1) chi(x) on a periodic grid;
+ *   find E curl-free with mean e and J = sigma E divergence-free; the effective
+ *   conductivity satisfies <J> = sigma_* <E> (isotropic case).
+ *   Green projection Gamma_1 (Eq. J11, J45) applied per frequency.
+ *   Schemes: Moulinec-Suquet (Eq. J0-0, J1), Eyre-Milton (Eq. J2), and both
+ *   applied in the substituted space H'' (Eq. J27-J44: J42a for MS, J43 for EM),
+ *   parameterised by the singularity interval [-beta, -alpha] of sigma_*(sigma_1)
+ *   through t(sigma_1) of Eq. J3.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an lsfft_status (0 = success) unless stated.
+ *   - Grids are d = 2 or 3 dimensional with n[a] points along axis a, where
+ *     n[0] is the fastest-varying (x) axis.  Each n[a] is a power of two in
+ *     [16, 8192] (3-D: [16, 512]).  N = n[0] n[1] (n[2]).
+ *   - Phase masks are uint8[N], x fastest (index x + n0*(y + n1*z)); a non-zero
+ *     byte marks phase 1 (conductivity sigma_1), zero marks the matrix (1).
+ *   - Fields are complex, component-planar: field[c][z][y][x], c = 0..d-1
+ *     (x, y, z components), interleaved (re, im) pairs of float (LSFFT_FP32)
+ *     or double (LSFFT_FP64).
+ *   - Objects returned through `out` pointers are owned by the caller and
+ *     released with the matching lsfft_free_result / lsfft_destroy_grid.
+ *   - All GPU work of a grid is issued on the CUDA stream given at creation;
+ *     for NULL the grid creates and owns a non-blocking stream (the iteration
+ *     is captured in CUDA graphs, which the legacy default stream does not
+ *     allow).  lsfft_solve returns after its work has completed.  A grid must
+ *     not be used from two host threads at once.
+ *   - Argument errors are detected on the host before any launch and return
+ *     LSFFT_EINVAL without touching device state.  CUDA failures return
+ *     LSFFT_ECUDA; lsfft_last_error() gives the CUDA message.
+ */
+#ifndef LSFFT_H
+#define LSFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSFFT_OK = 0,
+    LSFFT_EINVAL = 1,     /* invalid argument (checked before any launch)          */
+    LSFFT_ENOMEM = 2,     /* device or host allocation failed                      */
+    LSFFT_ENOTCONV = 3,   /* max_iter reached; result and history still returned   */
+    LSFFT_EDIVERGED = 4,  /* non-finite sigma_k or field norm grew by 1e12          */
+    LSFFT_ECUDA = 5       /* CUDA runtime error                                    */
+} lsfft_status;
+
+typedef enum { LSFFT_MS = 0, LSFFT_EM = 1, LSFFT_MS_SUB = 2, LSFFT_EM_SUB = 3 } lsfft_scheme;
+typedef enum { LSFFT_FP32 = 0, LSFFT_FP64 = 1 } lsfft_precision;
+/* Green symbol.  TRIG: Gamma(k) = k k^T/|k|^2 (Eq. J11) and Gamma = 0 at k = 0 and
+ * wherever a component sits at the Nyquist index -n/2.  FD: projection onto
+ * forward-difference gradients, u_a = exp(2 pi i k_a/n_a) - 1,
+ * Gamma(k) = u u^H/|u|^2 (the resistor-network picture of the section
+ * "Substitution at the level of the Hilbert space"). */
+typedef enum { LSFFT_GREEN_TRIG = 0, LSFFT_GREEN_FD = 1 } lsfft_green;
+
+typedef struct { double re, im; } lsfft_c128;
+
+typedef struct lsfft_grid lsfft_grid;
+
+typedef struct {
+    int scheme;            /* lsfft_scheme                                                  */
+    int precision;         /* lsfft_precision: arithmetic of fields and FFTs; reductions and
+                              the scalar recurrence are FP64 in both                        */
+    int green;             /* lsfft_green                                                   */
+    int max_iter;          /* maximum number of updates, >= 1                               */
+    int stop_consecutive;  /* K >= 1: stop once K successive relative sigma_* changes < tol */
+    int check_every;       /* updates per CUDA-graph launch between host checks, >= 1       */
+    double tol;            /* relative sigma_* change threshold (0 = run max_iter updates)  */
+    double alpha, beta;    /* pole interval [-beta,-alpha], 0 < alpha < beta; *_SUB only    */
+} lsfft_opts;
+
+typedef struct {
+    lsfft_c128 sigma_star;     /* sigma_* of the returned field: <J>.e / <E>.e              */
+    lsfft_c128 mean_E[3];      /* <E> of the returned field (d entries used)               */
+    lsfft_c128 mean_J[3];      /* <J> of the returned field                                */
+    int iters;                 /* number of updates applied                                 */
+    int status;                /* LSFFT_OK, LSFFT_ENOTCONV or LSFFT_EDIVERGED               */
+    int hist_len;              /* iters + 1 entries: iterate k = 0..iters                   */
+    double *hist_sigma_re;     /* host arrays of hist_len entries, owned by the result      */
+    double *hist_sigma_im;
+    double *hist_rel_change;   /* |sigma_k - sigma_{k-1}|/|sigma_k|; entry 0 is +inf        */
+    double *hist_field_norm;   /* <|E_k|^2>                                                 */
+    double solve_ms;           /* device time of the iteration (CUDA events), ms            */
+    int precision;             /* precision of E_device                                     */
+    int d;
+    int64_t n[3];
+    void *E_device;            /* complex [d][N] in `precision`, owned by the result        */
+} lsfft_result;
+
+/* Library version string, and the message of the last CUDA error seen on this
+ * host thread ("" if none). */
+const char *lsfft_version(void);
+const char *lsfft_last_error(void);
+const char *lsfft_strerror(int status);
+
+/* Create a grid: copies the host phase mask (N bytes, 1 = inclusion) to the
+ * device; the caller keeps its buffer.  `cuda_stream` is a cudaStream_t (may be
+ * NULL).  Problem statement of the introduction and Eq. J12: two phases, matrix
+ * conductivity 1, d = 2 or 3. */
+int lsfft_create_grid(int d, const int64_t n[3], const uint8_t *phase_mask_host,
+                      void *cuda_stream, lsfft_grid **out);
+
+/* Same, with the mask already on the device (N bytes, device pointer; copied on
+ * the grid's stream, so the caller must have finished writing it). */
+int lsfft_create_grid_device(int d, const int64_t n[3], const uint8_t *phase_mask_device,
+                             void *cuda_stream, lsfft_grid **out);
+
+/* Release every device buffer of the grid (after the stream has drained). */
+void lsfft_destroy_grid(lsfft_grid *grid);
+
+/* Fill `opts` with defaults: MS, FP32, TRIG, max_iter 1000, K = 3,
+ * check_every 8, tol 1e-6, alpha = beta = 0. */
+void lsfft_default_opts(lsfft_opts *opts);
+
+/* Solve Eq. J12/J13 for inclusion conductivity sigma_1 (complex) and applied
+ * field e (d real components, not all zero) with the chosen scheme.
+ * Returns LSFFT_OK, LSFFT_ENOTCONV or LSFFT_EDIVERGED with *out filled (the
+ * result exists in all three cases), or an error code with *out = NULL.
+ * Validation (EINVAL): scheme/precision/green out of range; max_iter < 1;
+ * stop_consecutive < 1; check_every < 1; tol < 0 or non-finite; non-finite
+ * sigma_1; e all zero; *_SUB with !(0 < alpha < beta) or sigma_1 = -alpha, -beta;
+ * MS with sigma_1 = -1 (reference medium 0); EM with sigma_1 = 0. */
+int lsfft_solve(lsfft_grid *grid, lsfft_c128 sigma1, const double *e,
+                const lsfft_opts *opts, lsfft_result **out);
+
+/* Copy the result's field E (complex [d][N] in the result's precision,
+ * d*N*(8 or 16) bytes) to `dst`: a host pointer if dst_on_device == 0, else a
+ * device pointer.  Synchronises the grid's stream. */
+int lsfft_copy_field(const lsfft_result *res, void *dst, int dst_on_device);
+
+/* Free the result's host history and device field. */
+void lsfft_free_result(lsfft_result *res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSFFT_H */

@@ -1,0 +1,278 @@
+"""GB300 (sm_103a) FFT Lippmann-Schwinger solver for two-phase periodic
+conductors, after G. W. Milton, "Substitution of subspace collections with
+nonorthogonal subspaces to accelerate Fast Fourier Transform methods applied to
+conducting composites" (arXiv 2001.08289).
+
+This package is a thin ctypes binding over the C ABI in include/lsfft.h
+(liblsfft.so, built in-tree by ``build.py``).  It only marshals arguments:
+every step of the iteration runs in the library's CUDA kernels.  Importing the
+package does not load the library; the first call does, and raises if the
+library is missing or cannot be loaded (there is no CPU fallback).
+
+The names follow the C ABI (lsfft_create_grid, lsfft_solve, ...); `Grid` and
+`solve` are convenience wrappers that manage the handles.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+__all__ = [
+    "MS", "EM", "MS_SUB", "EM_SUB", "FP32", "FP64", "GREEN_TRIG", "GREEN_FD",
+    "OK", "EINVAL", "ENOMEM", "ENOTCONV", "EDIVERGED", "ECUDA",
+    "LsfftError", "Opts", "Result", "Grid", "load_library", "library_path",
+    "lsfft_version", "lsfft_last_error", "lsfft_strerror", "lsfft_create_grid", "lsfft_create_grid_device",
+    "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
+    "SCHEMES", "GREENS",
+]
+
+MS, EM, MS_SUB, EM_SUB = 0, 1, 2, 3
+FP32, FP64 = 0, 1
+GREEN_TRIG, GREEN_FD = 0, 1
+OK, EINVAL, ENOMEM, ENOTCONV, EDIVERGED, ECUDA = 0, 1, 2, 3, 4, 5
+SCHEMES = {"ms": MS, "em": EM, "ms_sub": MS_SUB, "em_sub": EM_SUB}
+GREENS = {"trig": GREEN_TRIG, "fd": GREEN_FD}
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_PKG, "liblsfft.so")
+
+
+class LsfftError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lsfft status {status}: {message}")
+        self.status = status
+
+
+class _C128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class Opts(C.Structure):
+    """Mirror of lsfft_opts."""
+    _fields_ = [("scheme", C.c_int), ("precision", C.c_int), ("green", C.c_int), ("max_iter", C.c_int),
+                ("stop_consecutive", C.c_int), ("check_every", C.c_int), ("tol", C.c_double),
+                ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class _Result(C.Structure):
+    """Mirror of lsfft_result."""
+    _fields_ = [("sigma_star", _C128), ("mean_E", _C128 * 3), ("mean_J", _C128 * 3), ("iters", C.c_int),
+                ("status", C.c_int), ("hist_len", C.c_int), ("hist_sigma_re", C.POINTER(C.c_double)),
+                ("hist_sigma_im", C.POINTER(C.c_double)), ("hist_rel_change", C.POINTER(C.c_double)),
+                ("hist_field_norm", C.POINTER(C.c_double)), ("solve_ms", C.c_double), ("precision", C.c_int),
+                ("d", C.c_int), ("n", C.c_int64 * 3), ("E_device", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load liblsfft.so (once).  Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    lib.lsfft_version.restype = C.c_char_p
+    lib.lsfft_last_error.restype = C.c_char_p
+    lib.lsfft_strerror.restype = C.c_char_p
+    lib.lsfft_strerror.argtypes = [C.c_int]
+    lib.lsfft_create_grid.argtypes = [C.c_int, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.lsfft_create_grid_device.argtypes = lib.lsfft_create_grid.argtypes
+    lib.lsfft_destroy_grid.argtypes = [C.c_void_p]
+    lib.lsfft_destroy_grid.restype = None
+    lib.lsfft_default_opts.argtypes = [C.POINTER(Opts)]
+    lib.lsfft_default_opts.restype = None
+    lib.lsfft_solve.argtypes = [C.c_void_p, _C128, C.POINTER(C.c_double), C.POINTER(Opts),
+                                C.POINTER(C.POINTER(_Result))]
+    lib.lsfft_copy_field.argtypes = [C.POINTER(_Result), C.c_void_p, C.c_int]
+    lib.lsfft_free_result.argtypes = [C.POINTER(_Result)]
+    lib.lsfft_free_result.restype = None
+    _lib = lib
+    return lib
+
+
+# --- names of the C ABI -------------------------------------------------------
+
+def lsfft_version() -> str:
+    return load_library().lsfft_version().decode()
+
+
+def lsfft_last_error() -> str:
+    return load_library().lsfft_last_error().decode()
+
+
+def lsfft_strerror(status: int) -> str:
+    return load_library().lsfft_strerror(int(status)).decode()
+
+
+def _check(status: int, allowed=(OK,)):
+    if status not in allowed:
+        raise LsfftError(status, f"{lsfft_strerror(status)}: {lsfft_last_error()}")
+    return status
+
+
+def _dims(n):
+    arr = (C.c_int64 * 3)(1, 1, 1)
+    for i, v in enumerate(n):
+        arr[i] = int(v)
+    return arr
+
+
+def lsfft_create_grid(d: int, n, phase_mask_host: np.ndarray, stream: int = 0) -> int:
+    mask = np.ascontiguousarray(phase_mask_host, dtype=np.uint8)
+    h = C.c_void_p()
+    _check(load_library().lsfft_create_grid(int(d), _dims(n), mask.ctypes.data_as(C.c_void_p),
+                                            C.c_void_p(stream or None), C.byref(h)))
+    return h.value
+
+
+def lsfft_create_grid_device(d: int, n, mask_device_ptr: int, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load_library().lsfft_create_grid_device(int(d), _dims(n), C.c_void_p(mask_device_ptr),
+                                                   C.c_void_p(stream or None), C.byref(h)))
+    return h.value
+
+
+def lsfft_destroy_grid(grid: int) -> None:
+    load_library().lsfft_destroy_grid(C.c_void_p(grid))
+
+
+def lsfft_default_opts() -> Opts:
+    o = Opts()
+    load_library().lsfft_default_opts(C.byref(o))
+    return o
+
+
+def lsfft_solve(grid: int, sigma1: complex, e, opts: Opts):
+    """Returns (status, result pointer); the result exists for OK, ENOTCONV, EDIVERGED."""
+    s1 = complex(sigma1)
+    ev = (C.c_double * 3)(*[float(x) for x in list(e) + [0.0] * (3 - len(e))])
+    out = C.POINTER(_Result)()
+    st = load_library().lsfft_solve(C.c_void_p(grid), _C128(s1.real, s1.imag), ev, C.byref(opts), C.byref(out))
+    _check(st, (OK, ENOTCONV, EDIVERGED))
+    return st, out
+
+
+def lsfft_copy_field(res, dst_ptr: int, dst_on_device: bool) -> None:
+    _check(load_library().lsfft_copy_field(res, C.c_void_p(dst_ptr), int(bool(dst_on_device))))
+
+
+def lsfft_free_result(res) -> None:
+    load_library().lsfft_free_result(res)
+
+
+# --- convenience wrappers ----------------------------------------------------
+
+class Result:
+    """Host copy of a solve: sigma_*, averages, history; E on request."""
+
+    def __init__(self, status, ptr):
+        r = ptr.contents
+        self.status = int(status)
+        self.sigma_star = complex(r.sigma_star.re, r.sigma_star.im)
+        self.d = r.d
+        self.n = tuple(int(r.n[a]) for a in range(r.d))
+        self.mean_E = np.array([complex(r.mean_E[c].re, r.mean_E[c].im) for c in range(r.d)])
+        self.mean_J = np.array([complex(r.mean_J[c].re, r.mean_J[c].im) for c in range(r.d)])
+        self.iterations = int(r.iters)
+        L = int(r.hist_len)
+        self.hist_sigma = np.array([complex(r.hist_sigma_re[k], r.hist_sigma_im[k]) for k in range(L)])
+        self.hist_rel_change = np.array([r.hist_rel_change[k] for k in range(L)])
+        self.hist_field_norm = np.array([r.hist_field_norm[k] for k in range(L)])
+        self.solve_ms = float(r.solve_ms)
+        self.precision = int(r.precision)
+        self._ptr = ptr
+
+    def field_numpy(self) -> np.ndarray:
+        """E as a host complex array of shape (d, *reversed(n)) ([c][z][y][x])."""
+        dt = np.complex64 if self.precision == FP32 else np.complex128
+        out = np.empty((self.d,) + tuple(reversed(self.n)), dtype=dt)
+        lsfft_copy_field(self._ptr, out.ctypes.data, False)
+        return out
+
+    def field_into(self, dst_ptr: int) -> None:
+        """Copy E into device memory at dst_ptr (e.g. a torch tensor's data_ptr())."""
+        lsfft_copy_field(self._ptr, dst_ptr, True)
+
+    def free(self):
+        if self._ptr is not None:
+            lsfft_free_result(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def make_opts(scheme="ms", precision="fp32", green="trig", tol=1e-6, max_iter=1000, stop_consecutive=3,
+              check_every=8, alpha=0.0, beta=0.0) -> Opts:
+    o = lsfft_default_opts()
+    o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    o.precision = {"fp32": FP32, "fp64": FP64}[precision] if isinstance(precision, str) else int(precision)
+    o.green = GREENS[green] if isinstance(green, str) else int(green)
+    o.tol = float(tol)
+    o.max_iter = int(max_iter)
+    o.stop_consecutive = int(stop_consecutive)
+    o.check_every = int(check_every)
+    o.alpha = float(alpha)
+    o.beta = float(beta)
+    return o
+
+
+class Grid:
+    """A phase mask resident on the GPU (lsfft_create_grid / lsfft_destroy_grid).
+
+    mask: uint8 array of shape (n_y, n_x) or (n_z, n_y, n_x) (x fastest), on the
+    host (numpy) or on the device (a CUDA torch tensor).
+    """
+
+    def __init__(self, mask, stream: int = 0):
+        self.handle = None
+        shape = tuple(int(s) for s in mask.shape)
+        self.d = len(shape)
+        self.n = tuple(reversed(shape))
+        if hasattr(mask, "is_cuda") and mask.is_cuda:
+            import torch
+
+            self._mask_ref = mask.contiguous()
+            torch.cuda.current_stream().synchronize()
+            self.handle = lsfft_create_grid_device(self.d, self.n, self._mask_ref.data_ptr(), stream)
+        else:
+            m = np.asarray(mask)
+            if hasattr(mask, "numpy"):
+                m = mask.numpy()
+            self.handle = lsfft_create_grid(self.d, self.n, m, stream)
+        self.shape = shape
+        self.N = int(math.prod(shape))
+
+    def solve(self, sigma1, e, **kw) -> Result:
+        st, ptr = lsfft_solve(self.handle, sigma1, e, make_opts(**kw))
+        return Result(st, ptr)
+
+    def close(self):
+        if self.handle:
+            lsfft_destroy_grid(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

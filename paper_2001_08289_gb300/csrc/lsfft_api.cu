@@ -1,0 +1,696 @@
+// Host side of the C ABI declared in include/lsfft.h: argument checks, scheme
+// constants in FP64, workspace, the CUDA-graph iteration loop and results.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <complex>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "lsfft.h"
+#include "lsfft_kernels.cuh"
+#include "lsfft_misc.h"
+
+using namespace lsfft;
+using cplx = std::complex<double>;
+
+static thread_local std::string g_last_error;
+
+#define LSFFT_VERSION_STRING "lsfft-gb300 0.1 (sm_103a)"
+
+namespace {
+
+int fail_cuda(cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    g_last_error = buf;
+    return LSFFT_ECUDA;
+}
+
+#define CK(...)                                                    \
+    do {                                                           \
+        cudaError_t _e = (__VA_ARGS__);                            \
+        if (_e != cudaSuccess) return fail_cuda(_e, #__VA_ARGS__); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2i(int64_t v) {
+    int r = 0;
+    while ((int64_t(1) << r) < v) ++r;
+    return r;
+}
+void put(double (&dst)[2], cplx v) {
+    dst[0] = v.real();
+    dst[1] = v.imag();
+}
+
+struct GraphKey {
+    int precision, st, check_every;
+    bool operator<(const GraphKey& o) const {
+        return std::tie(precision, st, check_every) < std::tie(o.precision, o.st, o.check_every);
+    }
+};
+
+}  // namespace
+
+struct lsfft_grid {
+    int d = 0;
+    int64_t n[3] = {1, 1, 1};
+    int logn[3] = {0, 0, 0};
+    int64_t N = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;        // created by the library when the caller passed NULL
+    int device = 0;
+    int sm_count = 0;
+    uint8_t* mask = nullptr;
+    // workspace
+    int ws_prec = -1;
+    int ws_st = -1;                 // 0: Q only, 1: Q and S, 2: Q, S and T
+    void* X = nullptr;
+    void* S = nullptr;
+    void* T = nullptr;
+    double* partials = nullptr;
+    int64_t partials_cap = 0;
+    double* hist = nullptr;
+    int hist_cap = 0;
+    SchemeParams* prm_dev = nullptr;
+    SchemeParams* prm_host = nullptr;   // pinned
+    Ctrl* ctrl_dev = nullptr;
+    Ctrl* ctrl_host = nullptr;          // pinned
+    void* tw[3] = {nullptr, nullptr, nullptr};   // FP64 twiddles W_n^k per axis
+    void* fd[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // FD symbol per axis, FP32/FP64
+    bool prepared[2] = {false, false};
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+void clear_graphs(lsfft_grid* g) {
+    for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    g->graphs.clear();
+}
+
+int row_blocks(const lsfft_grid* g, int prec) {
+    Geom geo;
+    if (prec == LSFFT_FP32) {
+        if (g->d == 2) row_dispatch<float, 2>(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
+        else row_dispatch<float, 3>(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
+    } else {
+        if (g->d == 2) row_dispatch<double, 2>(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
+        else row_dispatch<double, 3>(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
+    }
+    const int64_t rows = g->N / g->n[0];
+    return (int)((rows + geo.per_block - 1) / geo.per_block);
+}
+
+template <typename T>
+bool col_supported(const lsfft_grid* g) {
+    for (int a = 1; a < g->d; ++a) {
+        Geom geo;
+        if (g->d == 2) col_dispatch<T, 2>(g->logn[a], OP_QUERY, nullptr, nullptr, &geo);
+        else col_dispatch<T, 3>(g->logn[a], OP_QUERY, nullptr, nullptr, &geo);
+        if (!geo.supported) return false;
+    }
+    return true;
+}
+
+template <typename T>
+int prepare_kernels(lsfft_grid* g) {
+    if (g->d == 2) {
+        CK(row_dispatch<T, 2>(g->logn[0], OP_PREPARE, nullptr, nullptr, nullptr));
+        CK(col_dispatch<T, 2>(g->logn[1], OP_PREPARE, nullptr, nullptr, nullptr));
+    } else {
+        CK(row_dispatch<T, 3>(g->logn[0], OP_PREPARE, nullptr, nullptr, nullptr));
+        CK(col_dispatch<T, 3>(g->logn[1], OP_PREPARE, nullptr, nullptr, nullptr));
+        CK(col_dispatch<T, 3>(g->logn[2], OP_PREPARE, nullptr, nullptr, nullptr));
+    }
+    return LSFFT_OK;
+}
+
+int ensure_workspace(lsfft_grid* g, int prec, int st, int max_iter) {
+    if (g->ws_prec != prec || g->ws_st < st) {
+        clear_graphs(g);
+        cudaFree(g->X);
+        cudaFree(g->S);
+        cudaFree(g->T);
+        g->X = g->S = g->T = nullptr;
+        g->ws_prec = -1;
+        const size_t bytes = (size_t)g->d * g->N * (prec == LSFFT_FP32 ? 8 : 16);
+        if (cudaMalloc(&g->X, bytes) != cudaSuccess) return fail_cuda(cudaErrorMemoryAllocation, "workspace X");
+        if (st >= 1 && cudaMalloc(&g->S, bytes) != cudaSuccess) return fail_cuda(cudaErrorMemoryAllocation, "workspace S");
+        if (st >= 2 && cudaMalloc(&g->T, bytes) != cudaSuccess) return fail_cuda(cudaErrorMemoryAllocation, "workspace T");
+        g->ws_prec = prec;
+        g->ws_st = st;
+    }
+    const int nb = row_blocks(g, prec);
+    const int64_t need = (int64_t)nb * (4 * g->d + 1);
+    if (need > g->partials_cap) {
+        clear_graphs(g);
+        cudaFree(g->partials);
+        g->partials = nullptr;
+        g->partials_cap = 0;
+        CK(cudaMalloc(&g->partials, need * sizeof(double)));
+        g->partials_cap = need;
+    }
+    if (max_iter + 1 > g->hist_cap) {
+        clear_graphs(g);
+        cudaFree(g->hist);
+        g->hist = nullptr;
+        g->hist_cap = 0;
+        CK(cudaMalloc(&g->hist, (size_t)(max_iter + 1) * HIST_STRIDE * sizeof(double)));
+        g->hist_cap = max_iter + 1;
+    }
+    return LSFFT_OK;
+}
+
+// Tables built in FP64 on the host: twiddles W_n^k = exp(-2 pi i k/n) and the
+// forward-difference symbol u(k) = exp(2 pi i k/n) - 1 = -2 sin^2(pi k/n) + i sin(2 pi k/n).
+int build_tables(lsfft_grid* g) {
+    for (int a = 0; a < g->d; ++a) {
+        const int64_t n = g->n[a];
+        double* tw = (double*)malloc(sizeof(double) * 2 * n);
+        double* fd64 = (double*)malloc(sizeof(double) * 2 * n);
+        float* fd32 = (float*)malloc(sizeof(float) * 2 * n);
+        if (!tw || !fd64 || !fd32) {
+            free(tw);
+            free(fd64);
+            free(fd32);
+            return LSFFT_ENOMEM;
+        }
+        for (int64_t k = 0; k < n; ++k) {
+            const double th = 2.0 * kPi * (double)k / (double)n;
+            tw[2 * k] = cos(th);
+            tw[2 * k + 1] = -sin(th);
+            const double h = sin(kPi * (double)k / (double)n);
+            fd64[2 * k] = -2.0 * h * h;
+            fd64[2 * k + 1] = sin(th);
+            fd32[2 * k] = (float)fd64[2 * k];
+            fd32[2 * k + 1] = (float)fd64[2 * k + 1];
+        }
+        int rc = LSFFT_OK;
+        if (cudaMalloc(&g->tw[a], sizeof(double) * 2 * n) != cudaSuccess ||
+            cudaMalloc(&g->fd[a][1], sizeof(double) * 2 * n) != cudaSuccess ||
+            cudaMalloc(&g->fd[a][0], sizeof(float) * 2 * n) != cudaSuccess)
+            rc = fail_cuda(cudaErrorMemoryAllocation, "tables");
+        if (rc == LSFFT_OK) {
+            cudaError_t e = cudaMemcpy(g->tw[a], tw, sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(g->fd[a][1], fd64, sizeof(double) * 2 * n, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(g->fd[a][0], fd32, sizeof(float) * 2 * n, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) rc = fail_cuda(e, "table upload");
+        }
+        free(tw);
+        free(fd64);
+        free(fd32);
+        if (rc != LSFFT_OK) return rc;
+    }
+    return LSFFT_OK;
+}
+
+int create_common(int d, const int64_t n[3], const uint8_t* mask, bool on_device, void* stream, lsfft_grid** out) {
+    if (!out || !n || !mask) {
+        g_last_error = "null argument";
+        return LSFFT_EINVAL;
+    }
+    *out = nullptr;
+    if (d != 2 && d != 3) {
+        g_last_error = "d must be 2 or 3";
+        return LSFFT_EINVAL;
+    }
+    const int64_t nmax = d == 2 ? 8192 : 512;
+    for (int a = 0; a < d; ++a) {
+        if (!is_pow2(n[a]) || n[a] < 16 || n[a] > nmax) {
+            g_last_error = "every n[a] must be a power of two in [16, 8192] (2-D) or [16, 512] (3-D)";
+            return LSFFT_EINVAL;
+        }
+    }
+    lsfft_grid* g = new (std::nothrow) lsfft_grid();
+    if (!g) return LSFFT_ENOMEM;
+    g->d = d;
+    g->N = 1;
+    for (int a = 0; a < d; ++a) {
+        g->n[a] = n[a];
+        g->logn[a] = ilog2i(n[a]);
+        g->N *= n[a];
+    }
+    g->stream = (cudaStream_t)stream;
+    int rc = LSFFT_OK;
+    cudaError_t e = cudaSuccess;
+    if (!g->stream) {
+        // CUDA graphs cannot be captured on the legacy default stream.
+        e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+        g->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess) e = cudaMalloc(&g->mask, (size_t)g->N);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->mask, mask, (size_t)g->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            g->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&g->prm_dev, sizeof(SchemeParams));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->prm_host, sizeof(SchemeParams));
+    if (e == cudaSuccess) e = cudaMalloc(&g->ctrl_dev, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMallocHost(&g->ctrl_host, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
+    if (e != cudaSuccess) rc = fail_cuda(e, "create_grid");
+    if (rc == LSFFT_OK) rc = build_tables(g);
+    if (rc == LSFFT_OK) {
+        e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) rc = fail_cuda(e, "create_grid sync");
+    }
+    if (rc != LSFFT_OK) {
+        lsfft_destroy_grid(g);
+        return rc;
+    }
+    *out = g;
+    return LSFFT_OK;
+}
+
+bool finite_c(cplx v) { return std::isfinite(v.real()) && std::isfinite(v.imag()); }
+
+// Scheme constants (FP64).  Returns an empty string if valid, else the reason.
+std::string build_params(const lsfft_grid* g, cplx s1, const double* e, const lsfft_opts* o, SchemeParams* P) {
+    memset(P, 0, sizeof(*P));
+    P->scheme = o->scheme;
+    P->green = o->green;
+    P->d = g->d;
+    P->max_iter = o->max_iter;
+    P->consecutive = o->stop_consecutive;
+    P->tol = o->tol;
+    P->inv_ntot = 1.0 / (double)g->N;
+    for (int c = 0; c < g->d; ++c) P->e[c] = e[c];
+    put(P->sigma1, s1);
+    const cplx one(1.0, 0.0);
+    switch (o->scheme) {
+        case LSFFT_MS: {   // Eq. J0-0 with sigma_0 = (sigma_1 + 1)/2 (Eq. J1)
+            const cplx s0 = (s1 + one) / 2.0;
+            if (s0 == 0.0) return "Moulinec-Suquet reference medium is 0 (sigma_1 = -1)";
+            put(P->a_in, s1 / s0 - one);
+            put(P->a_out, one / s0 - one);
+            put(P->g_b, cplx(-1.0));
+            put(P->g_ce, one);
+            put(P->iq_in, one);
+            put(P->iq_out, one);
+            break;
+        }
+        case LSFFT_EM: {   // reference sqrt(sigma_1) (Eq. J2)
+            const cplx s0 = std::sqrt(s1);
+            if (s0 == 0.0) return "Eyre-Milton is undefined at sigma_1 = 0";
+            put(P->a_in, (s1 - s0) / (s1 + s0));
+            put(P->a_out, (one - s0) / (one + s0));
+            put(P->inv2s0, one / (2.0 * s0));
+            put(P->g_a, one);
+            put(P->g_b, cplx(-2.0));
+            put(P->g_a0, one);
+            put(P->g_ce, 2.0 * s0);
+            put(P->iq_in, s1 + s0);
+            put(P->iq_out, one + s0);
+            break;
+        }
+        case LSFFT_MS_SUB:
+        case LSFFT_EM_SUB: {
+            const double al = o->alpha, be = o->beta;
+            if (!(al > 0.0 && be > al && std::isfinite(be))) return "substituted schemes need 0 < alpha < beta";
+            // p from Eq. J24 with p1^2 + p2^2 + p3^2 = 1; t from Eq. J3
+            const double dd = be - al;
+            const double p1sq = (1.0 + al) * (1.0 + be) / dd, p2sq = -(1.0 + al) / dd, p3sq = -al * (1.0 + be) / dd;
+            const cplx p1(sqrt(p1sq), 0.0), p2(0.0, sqrt(-p2sq)), p3(0.0, sqrt(-p3sq));
+            if (s1 + be == 0.0) return "sigma_1 = -beta maps to t = infinity";
+            const cplx t = (s1 + al) * (1.0 + be) / ((s1 + be) * (1.0 + al));
+            put(P->p1, p1);
+            put(P->p2, p2);
+            put(P->p3, p3);
+            put(P->tm1p1, (t - one) * p1);
+            if (o->scheme == LSFFT_MS_SUB) {   // Eq. J42a, reference (t + 1)/2
+                const cplx s0 = (t + one) / 2.0;
+                if (s0 == 0.0) return "MS in H'' reference medium is 0 (t = -1)";
+                put(P->k1, (t - one) * p1 / s0);
+                put(P->k2, (one - s0) / s0);
+                put(P->k3, (t - one) * p2 / s0);
+                put(P->g_b, cplx(-1.0));
+                put(P->g_ce, one);
+                put(P->iq_in, one);
+                put(P->iq_out, one);
+            } else {                           // Eq. J43, reference sqrt(t)
+                const cplx rt = std::sqrt(t);
+                if (rt == 0.0) return "sigma_1 = -alpha maps to t = 0";
+                put(P->w, (one - rt) / (one + rt));
+                put(P->inv2s0, one / (2.0 * rt));
+                put(P->g_a, one);
+                put(P->g_b, cplx(-2.0));
+                put(P->g_a0, one);
+                put(P->g_ce, 2.0 * rt);
+                put(P->iq_in, one + rt + (t - one) * p1 * p1);
+                put(P->iq_out, one + rt);
+                put(P->is_in, (t - one) * p1 * p2);
+                put(P->it_in, (t - one) * p1 * p3);
+            }
+            break;
+        }
+        default:
+            return "unknown scheme";
+    }
+    return "";
+}
+
+template <typename T>
+PassArgs<T> base_args(lsfft_grid* g, int st) {
+    PassArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    const int p = sizeof(T) == 4 ? 0 : 1;
+    A.X = (cx<T>*)g->X;
+    A.S = st >= 1 ? (cx<T>*)g->S : nullptr;
+    A.Tf = st >= 2 ? (cx<T>*)g->T : nullptr;
+    A.mask = g->mask;
+    A.prm = g->prm_dev;
+    A.ctrl = g->ctrl_dev;
+    A.partials = g->partials;
+    for (int a = 0; a < 3; ++a) A.fd[a] = a < g->d ? (const cx<T>*)g->fd[a][p] : nullptr;
+    A.Ntot = g->N;
+    for (int a = 0; a < 3; ++a) A.n[a] = (int)g->n[a];
+    return A;
+}
+
+template <typename T>
+cudaError_t launch_row(lsfft_grid* g, int st, int mode, cx<T>* Eout) {
+    PassArgs<T> A = base_args<T>(g, st);
+    A.Eout = Eout;
+    A.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[0] : nullptr;
+    A.n_lines = g->N / g->n[0];
+    A.mode = mode;
+    if (g->d == 2) return row_dispatch<T, 2>(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
+    return row_dispatch<T, 3>(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
+}
+
+template <typename T>
+cudaError_t launch_cols(lsfft_grid* g, int st) {
+    PassArgs<T> A = base_args<T>(g, st);
+    if (g->d == 2) {
+        A.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[1] : nullptr;
+        A.ls = g->n[0];
+        A.n_inner = g->n[0];
+        A.outer_stride = 0;
+        A.n_outer = 1;
+        A.line_axis = 1;
+        A.mode = MODE_COL_GAMMA;
+        return col_dispatch<T, 2>(g->logn[1], OP_LAUNCH, &A, g->stream, nullptr);
+    }
+    PassArgs<T> Y = A;
+    Y.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[1] : nullptr;
+    Y.ls = g->n[0];
+    Y.n_inner = g->n[0];
+    Y.outer_stride = g->n[0] * g->n[1];
+    Y.n_outer = g->n[2];
+    Y.line_axis = 1;
+    Y.mode = MODE_COL_FWD;
+    cudaError_t e = col_dispatch<T, 3>(g->logn[1], OP_LAUNCH, &Y, g->stream, nullptr);
+    if (e != cudaSuccess) return e;
+    PassArgs<T> Z = A;
+    Z.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[2] : nullptr;
+    Z.ls = g->n[0] * g->n[1];
+    Z.n_inner = g->n[0] * g->n[1];
+    Z.outer_stride = 0;
+    Z.n_outer = 1;
+    Z.line_axis = 2;
+    Z.mode = MODE_COL_GAMMA;
+    e = col_dispatch<T, 3>(g->logn[2], OP_LAUNCH, &Z, g->stream, nullptr);
+    if (e != cudaSuccess) return e;
+    Y.mode = MODE_COL_INV;
+    return col_dispatch<T, 3>(g->logn[1], OP_LAUNCH, &Y, g->stream, nullptr);
+}
+
+template <typename T>
+cudaError_t launch_iteration(lsfft_grid* g, int st, int nblocks, int row_mode) {
+    cudaError_t e = launch_row<T>(g, st, row_mode, nullptr);
+    if (e != cudaSuccess) return e;
+    e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, g->prm_dev, g->ctrl_dev, g->hist, 0, g->stream);
+    if (e != cudaSuccess) return e;
+    return launch_cols<T>(g, st);
+}
+
+template <typename T>
+int get_graph(lsfft_grid* g, int st, int nblocks, int check_every, cudaGraphExec_t* out) {
+    const GraphKey key{(int)sizeof(T), st, check_every};
+    auto it = g->graphs.find(key);
+    if (it != g->graphs.end()) {
+        *out = it->second;
+        return LSFFT_OK;
+    }
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < check_every && le == cudaSuccess; ++i) le = launch_iteration<T>(g, st, nblocks, MODE_ROW_ITER);
+    cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+    if (le != cudaSuccess) return fail_cuda(le, "graph capture launch");
+    if (ce != cudaSuccess) return fail_cuda(ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail_cuda(ie, "cudaGraphInstantiate");
+    g->graphs[key] = exec;
+    *out = exec;
+    return LSFFT_OK;
+}
+
+template <typename T>
+int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
+    if (!g->prepared[sizeof(T) == 8]) {
+        int rc = prepare_kernels<T>(g);
+        if (rc != LSFFT_OK) return rc;
+        g->prepared[sizeof(T) == 8] = true;
+    }
+    const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
+    cudaGraphExec_t exec;
+    int rc = get_graph<T>(g, st, nblocks, o->check_every, &exec);
+    if (rc != LSFFT_OK) return rc;
+
+    CK(cudaMemcpyAsync(g->prm_dev, g->prm_host, sizeof(SchemeParams), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemsetAsync(g->ctrl_dev, 0, sizeof(Ctrl), g->stream));
+    CK(cudaEventRecord(g->ev0, g->stream));
+    CK(launch_init<T>((cx<T>*)g->X, st >= 1 ? (cx<T>*)g->S : nullptr, st >= 2 ? (cx<T>*)g->T : nullptr, g->mask,
+                      g->prm_dev, g->N, g->d, g->sm_count, g->stream));
+    CK(launch_iteration<T>(g, st, nblocks, MODE_ROW_FIRST));
+    // Every finalize either sets `done` or advances the iteration count, so the
+    // loop ends after at most max_iter / check_every + 1 graph launches; the
+    // bound below only guards against kernels that silently did not run.
+    const int64_t max_launches = (int64_t)o->max_iter / o->check_every + 2;
+    for (int64_t launches = 0;; ++launches) {
+        CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        if (g->ctrl_host->done) break;
+        if (launches > max_launches) {
+            g_last_error = "iteration control block never reported completion";
+            return LSFFT_ECUDA;
+        }
+        CK(cudaGraphLaunch(exec, g->stream));
+    }
+    const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
+    void* E = nullptr;
+    CK(cudaMallocAsync(&E, ebytes, g->stream));
+    cudaError_t e = launch_row<T>(g, st, MODE_ROW_OUTPUT, (cx<T>*)E);
+    if (e == cudaSuccess)
+        e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, g->prm_dev, g->ctrl_dev, g->hist, 1, g->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev1, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(E, g->stream);
+        return fail_cuda(e, "solve");
+    }
+    const Ctrl& C = *g->ctrl_host;
+    res->E_device = E;
+    res->iters = C.iter;
+    res->status = C.status;
+    res->hist_len = C.iter + 1;
+    res->sigma_star.re = C.sigma[0];
+    res->sigma_star.im = C.sigma[1];
+    for (int c = 0; c < g->d; ++c) {
+        res->mean_E[c].re = C.meanE[c][0];
+        res->mean_E[c].im = C.meanE[c][1];
+        res->mean_J[c].re = C.meanJ[c][0];
+        res->mean_J[c].im = C.meanJ[c][1];
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+    res->solve_ms = ms;
+    const int L = res->hist_len;
+    double* h = (double*)malloc(sizeof(double) * HIST_STRIDE * L);
+    res->hist_sigma_re = (double*)malloc(sizeof(double) * L);
+    res->hist_sigma_im = (double*)malloc(sizeof(double) * L);
+    res->hist_rel_change = (double*)malloc(sizeof(double) * L);
+    res->hist_field_norm = (double*)malloc(sizeof(double) * L);
+    if (!h || !res->hist_sigma_re || !res->hist_sigma_im || !res->hist_rel_change || !res->hist_field_norm) {
+        free(h);
+        return LSFFT_ENOMEM;
+    }
+    e = cudaMemcpy(h, g->hist, sizeof(double) * HIST_STRIDE * L, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        free(h);
+        return fail_cuda(e, "history download");
+    }
+    for (int k = 0; k < L; ++k) {
+        res->hist_sigma_re[k] = h[HIST_STRIDE * k + 0];
+        res->hist_sigma_im[k] = h[HIST_STRIDE * k + 1];
+        res->hist_rel_change[k] = h[HIST_STRIDE * k + 2];
+        res->hist_field_norm[k] = h[HIST_STRIDE * k + 3];
+    }
+    free(h);
+    return LSFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lsfft_version(void) { return LSFFT_VERSION_STRING; }
+const char* lsfft_last_error(void) { return g_last_error.c_str(); }
+
+const char* lsfft_strerror(int status) {
+    switch (status) {
+        case LSFFT_OK: return "ok";
+        case LSFFT_EINVAL: return "invalid argument";
+        case LSFFT_ENOMEM: return "out of memory";
+        case LSFFT_ENOTCONV: return "not converged within max_iter";
+        case LSFFT_EDIVERGED: return "iteration diverged";
+        case LSFFT_ECUDA: return "CUDA error";
+        default: return "unknown status";
+    }
+}
+
+int lsfft_create_grid(int d, const int64_t n[3], const uint8_t* phase_mask_host, void* cuda_stream, lsfft_grid** out) {
+    return create_common(d, n, phase_mask_host, false, cuda_stream, out);
+}
+
+int lsfft_create_grid_device(int d, const int64_t n[3], const uint8_t* phase_mask_device, void* cuda_stream,
+                             lsfft_grid** out) {
+    return create_common(d, n, phase_mask_device, true, cuda_stream, out);
+}
+
+void lsfft_destroy_grid(lsfft_grid* g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    clear_graphs(g);
+    cudaFree(g->mask);
+    cudaFree(g->X);
+    cudaFree(g->S);
+    cudaFree(g->T);
+    cudaFree(g->partials);
+    cudaFree(g->hist);
+    cudaFree(g->prm_dev);
+    cudaFree(g->ctrl_dev);
+    if (g->prm_host) cudaFreeHost(g->prm_host);
+    if (g->ctrl_host) cudaFreeHost(g->ctrl_host);
+    for (int a = 0; a < 3; ++a) {
+        cudaFree(g->tw[a]);
+        cudaFree(g->fd[a][0]);
+        cudaFree(g->fd[a][1]);
+    }
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->own_stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+void lsfft_default_opts(lsfft_opts* o) {
+    if (!o) return;
+    o->scheme = LSFFT_MS;
+    o->precision = LSFFT_FP32;
+    o->green = LSFFT_GREEN_TRIG;
+    o->max_iter = 1000;
+    o->stop_consecutive = 3;
+    o->check_every = 8;
+    o->tol = 1e-6;
+    o->alpha = 0.0;
+    o->beta = 0.0;
+}
+
+int lsfft_solve(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_opts* o, lsfft_result** out) {
+    if (!out) {
+        g_last_error = "null out";
+        return LSFFT_EINVAL;
+    }
+    *out = nullptr;
+    if (!g || !e || !o) {
+        g_last_error = "null argument";
+        return LSFFT_EINVAL;
+    }
+    if (o->scheme < 0 || o->scheme > 3 || (o->precision != 0 && o->precision != 1) || (o->green != 0 && o->green != 1) ||
+        o->max_iter < 1 || o->stop_consecutive < 1 || o->check_every < 1 || !(o->tol >= 0.0) || !std::isfinite(o->tol)) {
+        g_last_error = "option out of range";
+        return LSFFT_EINVAL;
+    }
+    const cplx s1(sigma1.re, sigma1.im);
+    if (!finite_c(s1)) {
+        g_last_error = "sigma_1 must be finite";
+        return LSFFT_EINVAL;
+    }
+    double e2 = 0.0;
+    for (int c = 0; c < g->d; ++c) {
+        if (!std::isfinite(e[c])) {
+            g_last_error = "e must be finite";
+            return LSFFT_EINVAL;
+        }
+        e2 += e[c] * e[c];
+    }
+    if (e2 == 0.0) {
+        g_last_error = "e must not vanish";
+        return LSFFT_EINVAL;
+    }
+    const bool fp32 = o->precision == LSFFT_FP32;
+    if (!(fp32 ? col_supported<float>(g) : col_supported<double>(g))) {
+        g_last_error = "grid size not supported in this precision (FP64 2-D lines up to 4096)";
+        return LSFFT_EINVAL;
+    }
+    std::string why = build_params(g, s1, e, o, g->prm_host);
+    if (!why.empty()) {
+        g_last_error = why;
+        return LSFFT_EINVAL;
+    }
+    const int st = o->scheme == LSFFT_EM_SUB ? 2 : (o->scheme == LSFFT_MS_SUB ? 1 : 0);
+    int rc = ensure_workspace(g, o->precision, st, o->max_iter);
+    if (rc != LSFFT_OK) return rc;
+    lsfft_result* res = (lsfft_result*)calloc(1, sizeof(lsfft_result));
+    if (!res) return LSFFT_ENOMEM;
+    res->precision = o->precision;
+    res->d = g->d;
+    for (int a = 0; a < 3; ++a) res->n[a] = a < g->d ? g->n[a] : 1;
+    rc = fp32 ? run_solve<float>(g, o, st, res) : run_solve<double>(g, o, st, res);
+    if (rc != LSFFT_OK) {
+        lsfft_free_result(res);
+        return rc;
+    }
+    *out = res;
+    return res->status == ST_OK ? LSFFT_OK : res->status;
+}
+
+int lsfft_copy_field(const lsfft_result* res, void* dst, int dst_on_device) {
+    if (!res || !dst || !res->E_device) {
+        g_last_error = "null argument";
+        return LSFFT_EINVAL;
+    }
+    size_t N = 1;
+    for (int a = 0; a < res->d; ++a) N *= (size_t)res->n[a];
+    const size_t bytes = (size_t)res->d * N * (res->precision == LSFFT_FP32 ? 8 : 16);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(dst, res->E_device, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return LSFFT_OK;
+}
+
+void lsfft_free_result(lsfft_result* res) {
+    if (!res) return;
+    if (res->E_device) cudaFree(res->E_device);
+    free(res->hist_sigma_re);
+    free(res->hist_sigma_im);
+    free(res->hist_rel_change);
+    free(res->hist_field_norm);
+    free(res);
+}
+
+}  // extern "C"

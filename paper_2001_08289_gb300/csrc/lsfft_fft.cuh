@@ -1,0 +1,185 @@
+// Shared-memory Stockham FFT of one line, held in registers between stages.
+//
+// A line of N complex points (N a power of two) is owned by T_LINE = N/E
+// threads; thread t holds the elements with index t + T_LINE*m, m = 0..E-1,
+// in v[m].  fft_line<...>::run() returns, in the same layout, the unnormalised
+// DFT  X[k] = sum_j x[j] exp(-+2 pi i j k / N)  (forward sign -, inverse +).
+//
+// Stage s (radix R <= RMAX, NS = product of earlier radices): butterfly j
+// (0 <= j < N/R) takes x[j + r N/R], r = 0..R-1, multiplies leg r by
+// W_{NS R}^{(j mod NS) r}, forms a radix-R DFT in registers and writes leg r to
+// position (j / NS) NS R + (j mod NS) + r NS.  With thread t handling
+// j = t + T_LINE*i, its inputs are always x[t + T_LINE*m], so every stage reads
+// shared memory with unit stride across threads, and the last stage (NS R = N)
+// writes its outputs straight back into the thread's own registers in natural
+// order: no shared-memory pass after it.  Shared memory is padded with one
+// slot per 16 elements so that the strided writes of the first stage do not
+// collide in banks.
+//
+// Twiddles: FP32 uses sincospif() for W^{(j mod NS)} once per butterfly and
+// forms the other powers by balanced complex products; FP64 reads them from a
+// table W_N^k built on the host in double precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lsfft {
+
+template <typename T> struct CxOf;
+template <> struct CxOf<float> { using type = float2; };
+template <> struct CxOf<double> { using type = double2; };
+template <typename T> using cx = typename CxOf<T>::type;
+
+__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cneg(C a) { return mkc(-a.x, -a.y); }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return mkc(a.x * s, a.y * s); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return mkc(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+    return mkc(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mkc(a.x, -a.y); }
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+
+// cos and sin of 2 pi k / 16 (mathematical constants), written as a select
+// chain so that a compile-time k folds to a literal.
+__device__ __forceinline__ double cos16(int k) {
+    k &= 15;
+    const int m = k <= 8 ? k : 16 - k;             // cos is even
+    return m == 0 ? 1.0 : m == 1 ? 0.92387953251128675613 : m == 2 ? 0.70710678118654752440
+         : m == 3 ? 0.38268343236508977173 : m == 4 ? 0.0 : m == 5 ? -0.38268343236508977173
+         : m == 6 ? -0.70710678118654752440 : m == 7 ? -0.92387953251128675613 : -1.0;
+}
+__device__ __forceinline__ double sin16(int k) { return cos16(k + 12); }
+
+// a * exp(-+2 pi i q / 16), q a compile-time constant after unrolling.
+template <bool INV, typename C>
+__device__ __forceinline__ C mul_root16(C a, int q) {
+    using T = decltype(a.x);
+    q &= 15;
+    if (q == 0) return a;
+    if (q == 8) return cneg(a);
+    if (q == 4) return INV ? mkc(-a.y, a.x) : mkc(a.y, -a.x);
+    if (q == 12) return INV ? mkc(a.y, -a.x) : mkc(-a.y, a.x);
+    const T c = (T)cos16(q);
+    const T s = INV ? (T)sin16(q) : -(T)sin16(q);
+    if (q == 2 || q == 6 || q == 10 || q == 14) {
+        const T h = (T)0.70710678118654752440;
+        // c and s are +-h
+        const T cs = c > 0 ? h : -h, ss = s > 0 ? h : -h;
+        return mkc(cs * a.x - ss * a.y, cs * a.y + ss * a.x);
+    }
+    return mkc(c * a.x - s * a.y, c * a.y + s * a.x);
+}
+
+// In-register DFT of the R elements a[OFF + STRIDE*i] (R | 16) into out[0..R-1],
+// natural order, by recursive even/odd splitting; every index is a template
+// constant so the whole transform stays in registers.
+template <int R, int STRIDE, int OFF, bool INV, typename C, int NA>
+__device__ __forceinline__ void dft_rec(const C (&a)[NA], C (&out)[R]) {
+    if constexpr (R == 1) {
+        out[0] = a[OFF];
+    } else {
+        C ev[R / 2], od[R / 2];
+        dft_rec<R / 2, 2 * STRIDE, OFF, INV>(a, ev);
+        dft_rec<R / 2, 2 * STRIDE, OFF + STRIDE, INV>(a, od);
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const C t = mul_root16<INV>(od[k], k * (16 / R));
+            out[k] = cadd(ev[k], t);
+            out[k + R / 2] = csub(ev[k], t);
+        }
+    }
+}
+
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void dft(C (&a)[R]) {
+    C out[R];
+    dft_rec<R, 1, 0, INV>(a, out);
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = out[i];
+}
+
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+template <int N> struct LinePad { static constexpr int size = N + N / 16 + 1; };
+
+template <typename T, int N, int E, int RMAX, bool INV>
+struct LineFFT {
+    using C = cx<T>;
+    static constexpr int TL = N / E;   // threads per line
+    static_assert(N % E == 0, "E must divide N");
+
+    template <int R>
+    __device__ __forceinline__ static void twiddle(C (&a)[R], int jm, int span, const C* __restrict__ tw) {
+        // a[r] *= W_span^{jm r}, forward W = exp(-2 pi i / span)
+        if constexpr (sizeof(T) == 4) {
+            float s, c;
+            sincospif(2.0f * (float)jm / (float)span, &s, &c);
+            C w[R];
+            w[1] = mkc(c, INV ? s : -s);
+#pragma unroll
+            for (int r = 2; r < R; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
+#pragma unroll
+            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[r]);
+        } else {
+            const int step = (N / span) * jm;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = tw[step * r];
+                if (INV) w = cconj(w);
+                a[r] = cmul(a[r], w);
+            }
+        }
+    }
+
+    template <int NS>
+    __device__ __forceinline__ static void stage(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw) {
+        constexpr int REM = N / NS;
+        constexpr int R = REM >= RMAX ? RMAX : REM;
+        constexpr bool LAST = (NS * R == N);
+        constexpr int B = E / R;
+        static_assert(E % R == 0, "radix must divide E");
+        if constexpr (!LAST) __syncthreads();   // previous readers of sm are done
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int j = t + TL * i;
+            C a[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[r] = v[i + r * B];
+            if constexpr (NS > 1) twiddle<R>(a, j % NS, NS * R, tw);
+            dft<R, INV>(a);
+            if constexpr (LAST) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[i + r * B] = a[r];
+            } else {
+                const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+                for (int r = 0; r < R; ++r) sm[pad16(base + r * NS)] = a[r];
+            }
+        }
+        if constexpr (!LAST) {
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m)];
+            stage<NS * R>(v, sm, t, tw);
+        }
+    }
+
+    // Must be called by every thread of the block (it contains __syncthreads()
+    // whenever N > RMAX); threads of inactive lines pass dummy data.
+    __device__ __forceinline__ static void run(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw) {
+        stage<1>(v, sm, t, tw);
+    }
+};
+
+}  // namespace lsfft

@@ -1,0 +1,47 @@
+// Declarations of the launch helpers defined in lsfft_misc.cu and the
+// lsfft_inst_*.cu translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lsfft_fft.cuh"
+#include "lsfft_params.h"
+
+namespace lsfft {
+
+template <typename T> struct PassArgs;
+
+// Launch geometry reported by the dispatch functions.
+struct Geom {
+    int threads = 0;     // threads per block
+    int per_block = 0;   // rows (row pass) or line starts (strided pass) per block
+    int smem = 0;        // dynamic shared memory bytes
+    bool supported = false;
+};
+
+enum { OP_QUERY = 0, OP_PREPARE = 1, OP_LAUNCH = 2 };
+
+template <typename T>
+cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams* prm, int64_t Ntot,
+                        int d, int sm_count, cudaStream_t s);
+
+cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams* prm, Ctrl* ctrl,
+                            double* hist, int final_mode, cudaStream_t s);
+
+}  // namespace lsfft
+
+namespace lsfft {
+// Defined in the lsfft_inst_*.cu translation units.
+template <typename T, int D>
+cudaError_t row_dispatch(int logn, int op, const PassArgs<T>* A, cudaStream_t s, Geom* g);
+template <typename T, int D>
+cudaError_t col_dispatch(int logn, int op, const PassArgs<T>* A, cudaStream_t s, Geom* g);
+template <> cudaError_t row_dispatch<float, 2>(int, int, const PassArgs<float>*, cudaStream_t, Geom*);
+template <> cudaError_t row_dispatch<float, 3>(int, int, const PassArgs<float>*, cudaStream_t, Geom*);
+template <> cudaError_t row_dispatch<double, 2>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
+template <> cudaError_t row_dispatch<double, 3>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
+template <> cudaError_t col_dispatch<float, 2>(int, int, const PassArgs<float>*, cudaStream_t, Geom*);
+template <> cudaError_t col_dispatch<float, 3>(int, int, const PassArgs<float>*, cudaStream_t, Geom*);
+template <> cudaError_t col_dispatch<double, 2>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
+template <> cudaError_t col_dispatch<double, 3>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
+}  // namespace lsfft

@@ -1,0 +1,60 @@
+"""CPU checks of the C ABI library: it builds, loads without a GPU and exports
+every function declared in include/*.h; argument checks that precede any CUDA
+call work without a device."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(lsfft_\w+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2001_08289_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("lsfft_create_grid", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
+                     "lsfft_destroy_grid", "lsfft_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strings_without_gpu(lib):
+    lib.lsfft_strerror.restype = ctypes.c_char_p
+    lib.lsfft_version.restype = ctypes.c_char_p
+    assert lib.lsfft_strerror(1) == b"invalid argument"
+    assert b"sm_103a" in lib.lsfft_version()
+
+
+def test_create_grid_rejects_bad_shapes_before_touching_cuda(lib):
+    import paper_2001_08289_gb300 as L
+
+    L.load_library()
+    for d, n in [(4, (16, 16, 16)), (2, (15, 16)), (2, (16, 8)), (2, (16384, 16)), (3, (1024, 16, 16))]:
+        with pytest.raises(L.LsfftError) as ei:
+            L.lsfft_create_grid(d, n, np.zeros(int(np.prod(n)), np.uint8))
+        assert ei.value.status == L.EINVAL
