@@ -92,6 +92,7 @@ typedef struct {
     double *hist_rel_change;   /* |sigma_k - sigma_{k-1}|/|sigma_k|; entry 0 is +inf        */
     double *hist_field_norm;   /* <|E_k|^2>                                                 */
     double solve_ms;           /* device time of the iteration (CUDA events), ms            */
+    int64_t kernel_launches;   /* kernels this solve launched (no-op launches included)     */
     int precision;             /* precision of E_device                                     */
     int d;
     int64_t n[3];
@@ -141,6 +142,22 @@ int lsfft_copy_field(const lsfft_result *res, void *dst, int dst_on_device);
 
 /* Free the result's host history and device field. */
 void lsfft_free_result(lsfft_result *res);
+
+/* Diagnostics and benchmarking: set up the state of a solve (constants of
+ * Eq. J1/J2/J3/J24, the initial field and one full update, exactly as
+ * lsfft_solve starts) and return without further iterations.  Same arguments
+ * and validation as lsfft_solve.  Synchronises the grid's stream. */
+int lsfft_prepare(lsfft_grid *grid, lsfft_c128 sigma1, const double *e, const lsfft_opts *opts);
+
+/* After lsfft_prepare: enqueue `count` launches of one pass kind on the grid's
+ * stream and return without waiting.  kind 0: row pass (inverse x-DFT, scheme
+ * update with its volume-average partial sums, forward x-DFT); kind 1: the
+ * strided pass(es) of one update (2-D: y forward-Gamma-inverse; 3-D: y
+ * forward, z forward-Gamma-inverse, y inverse); kind 2: both, i.e. one update
+ * without the one-block FP64 finalize.  The passes keep iterating the prepared
+ * state in place; no stop test runs.  Returns EINVAL for an unknown kind,
+ * count < 0, or a grid without a prepared state (or whose last solve stopped). */
+int lsfft_launch_passes(lsfft_grid *grid, int kind, int count);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,7 @@ __all__ = [
     "LsfftError", "Opts", "Result", "Grid", "load_library", "library_path",
     "lsfft_version", "lsfft_last_error", "lsfft_strerror", "lsfft_create_grid", "lsfft_create_grid_device",
     "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
+    "lsfft_prepare", "lsfft_launch_passes", "make_opts",
     "SCHEMES", "GREENS",
 ]
 
@@ -65,7 +66,8 @@ class _Result(C.Structure):
     _fields_ = [("sigma_star", _C128), ("mean_E", _C128 * 3), ("mean_J", _C128 * 3), ("iters", C.c_int),
                 ("status", C.c_int), ("hist_len", C.c_int), ("hist_sigma_re", C.POINTER(C.c_double)),
                 ("hist_sigma_im", C.POINTER(C.c_double)), ("hist_rel_change", C.POINTER(C.c_double)),
-                ("hist_field_norm", C.POINTER(C.c_double)), ("solve_ms", C.c_double), ("precision", C.c_int),
+                ("hist_field_norm", C.POINTER(C.c_double)), ("solve_ms", C.c_double),
+                ("kernel_launches", C.c_int64), ("precision", C.c_int),
                 ("d", C.c_int), ("n", C.c_int64 * 3), ("E_device", C.c_void_p)]
 
 
@@ -96,6 +98,8 @@ def load_library():
     lib.lsfft_copy_field.argtypes = [C.POINTER(_Result), C.c_void_p, C.c_int]
     lib.lsfft_free_result.argtypes = [C.POINTER(_Result)]
     lib.lsfft_free_result.restype = None
+    lib.lsfft_prepare.argtypes = [C.c_void_p, _C128, C.POINTER(C.c_double), C.POINTER(Opts)]
+    lib.lsfft_launch_passes.argtypes = [C.c_void_p, C.c_int, C.c_int]
     _lib = lib
     return lib
 
@@ -170,6 +174,16 @@ def lsfft_free_result(res) -> None:
     load_library().lsfft_free_result(res)
 
 
+def lsfft_prepare(grid: int, sigma1: complex, e, opts: Opts) -> None:
+    s1 = complex(sigma1)
+    ev = (C.c_double * 3)(*[float(x) for x in list(e) + [0.0] * (3 - len(e))])
+    _check(load_library().lsfft_prepare(C.c_void_p(grid), _C128(s1.real, s1.imag), ev, C.byref(opts)))
+
+
+def lsfft_launch_passes(grid: int, kind: int, count: int) -> None:
+    _check(load_library().lsfft_launch_passes(C.c_void_p(grid), int(kind), int(count)))
+
+
 # --- convenience wrappers ----------------------------------------------------
 
 class Result:
@@ -189,6 +203,7 @@ class Result:
         self.hist_rel_change = np.array([r.hist_rel_change[k] for k in range(L)])
         self.hist_field_norm = np.array([r.hist_field_norm[k] for k in range(L)])
         self.solve_ms = float(r.solve_ms)
+        self.kernel_launches = int(r.kernel_launches)
         self.precision = int(r.precision)
         self._ptr = ptr
 
@@ -259,6 +274,12 @@ class Grid:
     def solve(self, sigma1, e, **kw) -> Result:
         st, ptr = lsfft_solve(self.handle, sigma1, e, make_opts(**kw))
         return Result(st, ptr)
+
+    def prepare(self, sigma1, e, **kw) -> None:
+        lsfft_prepare(self.handle, sigma1, e, make_opts(**kw))
+
+    def launch_passes(self, kind: int, count: int) -> None:
+        lsfft_launch_passes(self.handle, kind, count)
 
     def close(self):
         if self.handle:

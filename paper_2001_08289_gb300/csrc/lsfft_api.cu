@@ -86,6 +86,8 @@ struct lsfft_grid {
     void* tw[3] = {nullptr, nullptr, nullptr};   // FP64 twiddles W_n^k per axis
     void* fd[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // FD symbol per axis, FP32/FP64
     bool prepared[2] = {false, false};
+    int bench_prec = -1;            // precision of the state set up by lsfft_prepare (-1: none)
+    int bench_st = 0;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -460,27 +462,46 @@ int get_graph(lsfft_grid* g, int st, int nblocks, int check_every, cudaGraphExec
 }
 
 template <typename T>
-int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
+int ensure_prepared(lsfft_grid* g) {
     if (!g->prepared[sizeof(T) == 8]) {
         int rc = prepare_kernels<T>(g);
         if (rc != LSFFT_OK) return rc;
         g->prepared[sizeof(T) == 8] = true;
     }
-    const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
-    cudaGraphExec_t exec;
-    int rc = get_graph<T>(g, st, nblocks, o->check_every, &exec);
-    if (rc != LSFFT_OK) return rc;
+    return LSFFT_OK;
+}
 
+// Upload the constants, write the initial state and run the first update.
+template <typename T>
+int start_solve(lsfft_grid* g, int st) {
+    int rc0 = ensure_prepared<T>(g);
+    if (rc0 != LSFFT_OK) return rc0;
+    const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
     CK(cudaMemcpyAsync(g->prm_dev, g->prm_host, sizeof(SchemeParams), cudaMemcpyHostToDevice, g->stream));
     CK(cudaMemsetAsync(g->ctrl_dev, 0, sizeof(Ctrl), g->stream));
     CK(cudaEventRecord(g->ev0, g->stream));
     CK(launch_init<T>((cx<T>*)g->X, st >= 1 ? (cx<T>*)g->S : nullptr, st >= 2 ? (cx<T>*)g->T : nullptr, g->mask,
                       g->prm_dev, g->N, g->d, g->sm_count, g->stream));
     CK(launch_iteration<T>(g, st, nblocks, MODE_ROW_FIRST));
+    return LSFFT_OK;
+}
+
+template <typename T>
+int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
+    const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
+    int rc = ensure_prepared<T>(g);   // shared-memory limits must be set before capture
+    if (rc != LSFFT_OK) return rc;
+    cudaGraphExec_t exec;
+    rc = get_graph<T>(g, st, nblocks, o->check_every, &exec);
+    if (rc != LSFFT_OK) return rc;
+    rc = start_solve<T>(g, st);
+    if (rc != LSFFT_OK) return rc;
     // Every finalize either sets `done` or advances the iteration count, so the
     // loop ends after at most max_iter / check_every + 1 graph launches; the
     // bound below only guards against kernels that silently did not run.
     const int64_t max_launches = (int64_t)o->max_iter / o->check_every + 2;
+    const int per_iter = g->d == 2 ? 3 : 5;   // row pass, finalize, strided pass(es)
+    int64_t kernels = 1 + per_iter;           // init + first update
     for (int64_t launches = 0;; ++launches) {
         CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
         CK(cudaStreamSynchronize(g->stream));
@@ -490,7 +511,9 @@ int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
             return LSFFT_ECUDA;
         }
         CK(cudaGraphLaunch(exec, g->stream));
+        kernels += (int64_t)per_iter * o->check_every;
     }
+    kernels += 2;                             // output row pass and final finalize
     const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
     void* E = nullptr;
     CK(cudaMallocAsync(&E, ebytes, g->stream));
@@ -520,6 +543,7 @@ int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, g->ev0, g->ev1);
     res->solve_ms = ms;
+    res->kernel_launches = kernels;
     const int L = res->hist_len;
     double* h = (double*)malloc(sizeof(double) * HIST_STRIDE * L);
     res->hist_sigma_re = (double*)malloc(sizeof(double) * L);
@@ -611,12 +635,11 @@ void lsfft_default_opts(lsfft_opts* o) {
     o->beta = 0.0;
 }
 
-int lsfft_solve(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_opts* o, lsfft_result** out) {
-    if (!out) {
-        g_last_error = "null out";
-        return LSFFT_EINVAL;
-    }
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+// Shared argument checks and set-up of lsfft_solve and lsfft_prepare.
+int check_and_setup(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_opts* o, int* st_out) {
     if (!g || !e || !o) {
         g_last_error = "null argument";
         return LSFFT_EINVAL;
@@ -654,8 +677,24 @@ int lsfft_solve(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_o
         return LSFFT_EINVAL;
     }
     const int st = o->scheme == LSFFT_EM_SUB ? 2 : (o->scheme == LSFFT_MS_SUB ? 1 : 0);
-    int rc = ensure_workspace(g, o->precision, st, o->max_iter);
+    *st_out = st;
+    g->bench_prec = -1;
+    return ensure_workspace(g, o->precision, st, o->max_iter);
+}
+}  // namespace
+
+extern "C" {
+
+int lsfft_solve(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_opts* o, lsfft_result** out) {
+    if (!out) {
+        g_last_error = "null out";
+        return LSFFT_EINVAL;
+    }
+    *out = nullptr;
+    int st = 0;
+    int rc = check_and_setup(g, sigma1, e, o, &st);
     if (rc != LSFFT_OK) return rc;
+    const bool fp32 = o->precision == LSFFT_FP32;
     lsfft_result* res = (lsfft_result*)calloc(1, sizeof(lsfft_result));
     if (!res) return LSFFT_ENOMEM;
     res->precision = o->precision;
@@ -680,6 +719,37 @@ int lsfft_copy_field(const lsfft_result* res, void* dst, int dst_on_device) {
     const size_t bytes = (size_t)res->d * N * (res->precision == LSFFT_FP32 ? 8 : 16);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(dst, res->E_device, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return LSFFT_OK;
+}
+
+int lsfft_prepare(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_opts* o) {
+    int st = 0;
+    int rc = check_and_setup(g, sigma1, e, o, &st);
+    if (rc != LSFFT_OK) return rc;
+    rc = o->precision == LSFFT_FP32 ? start_solve<float>(g, st) : start_solve<double>(g, st);
+    if (rc != LSFFT_OK) return rc;
+    CK(cudaStreamSynchronize(g->stream));
+    g->bench_prec = o->precision;
+    g->bench_st = st;
+    return LSFFT_OK;
+}
+
+int lsfft_launch_passes(lsfft_grid* g, int kind, int count) {
+    if (!g || kind < 0 || kind > 2 || count < 0 || g->bench_prec < 0) {
+        g_last_error = "lsfft_launch_passes: bad kind/count or no prepared state";
+        return LSFFT_EINVAL;
+    }
+    for (int i = 0; i < count; ++i) {
+        cudaError_t e = cudaSuccess;
+        if (g->bench_prec == LSFFT_FP32) {
+            if (kind != 1) e = launch_row<float>(g, g->bench_st, MODE_ROW_ITER, nullptr);
+            if (e == cudaSuccess && kind != 0) e = launch_cols<float>(g, g->bench_st);
+        } else {
+            if (kind != 1) e = launch_row<double>(g, g->bench_st, MODE_ROW_ITER, nullptr);
+            if (e == cudaSuccess && kind != 0) e = launch_cols<double>(g, g->bench_st);
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "lsfft_launch_passes");
+    }
     return LSFFT_OK;
 }
 

@@ -75,11 +75,39 @@ def test_parity_2d_sizes(L, n, prec):
         _compare(L, square_array_mask(n), 100.0, np.array([1.0, 0.0]), scheme, "trig", prec, 10)
 
 
+@pytest.mark.parametrize("shape", [(16, 8192), (8192, 16), (32, 4096), (4096, 32), (64, 2048), (2048, 64),
+                                   (1024, 1024)])
+def test_parity_2d_long_lines(L, shape):
+    """Thin grids put every line length up to 8192 on both the row and the strided
+    pass (the kernels with the largest shared-memory and register footprints)."""
+    mask = random_mask(shape, 0.25, seed=sum(shape))
+    e = np.array([1.0, 0.0])
+    precs = ["fp32"] + (["fp64"] if max(shape) <= 4096 or shape[1] == 8192 else [])
+    for prec in precs:
+        for scheme in ("ms", "em_sub"):
+            _compare(L, mask, 10.0, e, scheme, "fd", prec, 6, ab=(0.05, 20.0))
+
+
+def test_fp64_rejects_8192_columns(L):
+    with L.Grid(np.zeros((8192, 16), np.uint8)) as g:
+        with pytest.raises(L.LsfftError) as ei:
+            g.solve(2.0, [1.0, 0.0], precision="fp64")
+        assert ei.value.status == L.EINVAL
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("scheme", ["ms", "em", "ms_sub", "em_sub"])
 def test_parity_3d(L, scheme, prec):
     mask = square_array_mask(16, d=3)
     _compare(L, mask, 5.0, np.array([1.0, 0.0, 0.0]), scheme, "trig", prec, 10)
+
+
+def test_parity_3d_512_lines(L):
+    """Line length 512 on all three axes' kernels via thin 3-D grids."""
+    for shape in ((16, 16, 512), (16, 512, 16), (512, 16, 16)):
+        mask = random_mask(shape, 0.2, seed=7)
+        for prec in ("fp32", "fp64"):
+            _compare(L, mask, 5.0, np.array([1.0, 0.0, 0.0]), "ms", "trig", prec, 5)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
