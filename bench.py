@@ -121,17 +121,21 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # roofline helpers
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(kind, scheme, N, d=2, fraction=FRACTION, cbytes=8):
-    """Bytes a pass must move per launch (complex FP32 fields, 1-byte mask).
+def algorithmic_bytes(kind, scheme, N, d=2, fraction=FRACTION, cbytes=8, packed=False):
+    """Bytes a pass must move per launch (FP32 fields, 1-byte mask).
 
-    row pass: read + write the Q field (2 d cbytes) and read the mask (1 B); the
-    substituted schemes also read + write S (and T) on phase-1 voxels only.
+    Complex layout: each of the d components is a complex plane (cbytes per
+    voxel).  Packed real layout (2-D, real coefficients): the d = 2 real
+    components share one complex plane, so the field costs cbytes per voxel.
+    row pass: read + write the Q field and read the mask (1 B); the substituted
+    schemes also read + write S (and T) on phase-1 voxels only.
     strided pass: read + write the Q field.
     """
+    per_field = cbytes if packed else d * cbytes
     if kind == "row":
-        extra = {"ms": 0, "em": 0, "ms_sub": 2, "em_sub": 4}[scheme] * d * cbytes * fraction
-        return N * (2 * d * cbytes + 1 + extra)
-    return N * 2 * d * cbytes
+        extra = {"ms": 0, "em": 0, "ms_sub": 2, "em_sub": 4}[scheme] * per_field * fraction
+        return N * (2 * per_field + 1 + extra)
+    return N * 2 * per_field
 
 
 def kernel_source_hash():
@@ -248,11 +252,14 @@ def run_ours(args, sigmas):
     e = [1.0, 0.0]
     kw = dict(precision="fp32", green=args.green, tol=TOL, max_iter=500, alpha=ALPHA_BETA[0], beta=ALPHA_BETA[1])
 
+    layout = {"packed": False}
+
     def step(g):
         out = []
         for s1 in sigmas:
             for sch in SCHEMES:
                 r = g.solve(s1, e, scheme=sch, **kw)
+                layout["packed"] = r.packed
                 out.append((s1, sch, r.iterations, r.status, r.sigma_star, r.solve_ms, r.kernel_launches))
                 r.free()
         return out
@@ -311,13 +318,13 @@ def run_ours(args, sigmas):
                 b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / args.pass_reps
-            byt = algorithmic_bytes(name, sch, N)
+            byt = algorithmic_bytes(name, sch, N, packed=layout["packed"])
             passes[f"{name}_pass|{sch}"] = {"ms": round(ms, 4), "alg_bytes": int(byt),
                                             "GBps": round(byt / ms / 1e6, 1),
                                             "frac_of_measured_hbm": round(byt / ms / 1e6 / peak, 4)}
     dom = max(("row_pass|ms", "col_pass|ms"), key=lambda k: passes[k]["ms"])
     kname = dom.split("|")[0]
-    wl = f"{n}x{n}_ms_fp32"
+    wl = f"{n}x{n}_ms_fp32_{'packed' if layout['packed'] else 'complex'}"
     roof = {"bound": "hbm", "kernel": kname, "achieved": passes[dom]["GBps"], "peak": peak, "unit": "GB/s",
             "frac": passes[dom]["frac_of_measured_hbm"], "traffic": ncu_traffic(kname, wl),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
@@ -358,7 +365,9 @@ def run_ours(args, sigmas):
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if layout["packed"] else "c64",
+            "data": "synthetic", "layout": "packed real (E_x + i E_y in one complex plane)" if layout["packed"]
+            else "complex component planes",
             "config": workload_config(args, sigmas), "roofline": roof, "gpu_launches": int(launches),
             "clocks": clk, "e2e": e2e, "time_to_tol": {"per_sigma1": per, "ms_over_em_sub_time_ratio": speed},
             "passes": passes}

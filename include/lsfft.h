@@ -19,7 +19,8 @@
  *   - Every function returns an lsfft_status (0 = success) unless stated.
  *   - Grids are d = 2 or 3 dimensional with n[a] points along axis a, where
  *     n[0] is the fastest-varying (x) axis.  Each n[a] is a power of two in
- *     [16, 8192] (3-D: [16, 512]).  N = n[0] n[1] (n[2]).
+ *     [16, 8192] (3-D: [16, 512]); in LSFFT_FP64 each n[a] <= 4096.
+ *     N = n[0] n[1] (n[2]).
  *   - Phase masks are uint8[N], x fastest (index x + n0*(y + n1*z)); a non-zero
  *     byte marks phase 1 (conductivity sigma_1), zero marks the matrix (1).
  *   - Fields are complex, component-planar: field[c][z][y][x], c = 0..d-1
@@ -93,6 +94,9 @@ typedef struct {
     double *hist_field_norm;   /* <|E_k|^2>                                                 */
     double solve_ms;           /* device time of the iteration (CUDA events), ms            */
     int64_t kernel_launches;   /* kernels this solve launched (no-op launches included)     */
+    int packed;                /* 1 if the packed real layout was used: 2-D with every scheme
+                                  coefficient real (real sigma_1, real reference medium); the
+                                  two real components then share one complex plane         */
     int precision;             /* precision of E_device                                     */
     int d;
     int64_t n[3];

@@ -67,7 +67,7 @@ class _Result(C.Structure):
                 ("status", C.c_int), ("hist_len", C.c_int), ("hist_sigma_re", C.POINTER(C.c_double)),
                 ("hist_sigma_im", C.POINTER(C.c_double)), ("hist_rel_change", C.POINTER(C.c_double)),
                 ("hist_field_norm", C.POINTER(C.c_double)), ("solve_ms", C.c_double),
-                ("kernel_launches", C.c_int64), ("precision", C.c_int),
+                ("kernel_launches", C.c_int64), ("packed", C.c_int), ("precision", C.c_int),
                 ("d", C.c_int), ("n", C.c_int64 * 3), ("E_device", C.c_void_p)]
 
 
@@ -204,6 +204,7 @@ class Result:
         self.hist_field_norm = np.array([r.hist_field_norm[k] for k in range(L)])
         self.solve_ms = float(r.solve_ms)
         self.kernel_launches = int(r.kernel_launches)
+        self.packed = bool(r.packed)
         self.precision = int(r.precision)
         self._ptr = ptr
 

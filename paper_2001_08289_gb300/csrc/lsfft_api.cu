@@ -79,13 +79,13 @@ struct lsfft_grid {
     int64_t partials_cap = 0;
     double* hist = nullptr;
     int hist_cap = 0;
-    SchemeParams* prm_dev = nullptr;
-    SchemeParams* prm_host = nullptr;   // pinned
+    SchemeParams* prm_host = nullptr;   // constants of the current solve (kernel parameters)
     Ctrl* ctrl_dev = nullptr;
     Ctrl* ctrl_host = nullptr;          // pinned
     void* tw[3] = {nullptr, nullptr, nullptr};   // FP64 twiddles W_n^k per axis
     void* fd[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // FD symbol per axis, FP32/FP64
     bool prepared[2] = {false, false};
+    int packed = 0;                 // packed real layout for the current solve
     int bench_prec = -1;            // precision of the state set up by lsfft_prepare (-1: none)
     int bench_st = 0;
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -99,7 +99,7 @@ void clear_graphs(lsfft_grid* g) {
     g->graphs.clear();
 }
 
-int row_blocks(const lsfft_grid* g, int prec) {
+Geom row_geom(const lsfft_grid* g, int prec) {
     Geom geo;
     if (prec == LSFFT_FP32) {
         if (g->d == 2) row_dispatch<float, 2>(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
@@ -108,12 +108,25 @@ int row_blocks(const lsfft_grid* g, int prec) {
         if (g->d == 2) row_dispatch<double, 2>(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
         else row_dispatch<double, 3>(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
     }
+    return geo;
+}
+
+int64_t persistent_blocks(const lsfft_grid* g, int64_t n_items, int blocks_per_sm) {
+    const int64_t cap = (int64_t)g->sm_count * (blocks_per_sm > 0 ? blocks_per_sm : 1);
+    return n_items < cap ? n_items : cap;
+}
+
+// Number of row-pass blocks (= partial-sum rows), valid after the kernels were prepared.
+int row_blocks(const lsfft_grid* g, int prec) {
+    const Geom geo = row_geom(g, prec);
     const int64_t rows = g->N / g->n[0];
-    return (int)((rows + geo.per_block - 1) / geo.per_block);
+    return (int)persistent_blocks(g, (rows + geo.per_block - 1) / geo.per_block, geo.blocks_per_sm);
 }
 
 template <typename T>
 bool col_supported(const lsfft_grid* g) {
+    Geom rg = row_geom(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
+    if (!rg.supported) return false;
     for (int a = 1; a < g->d; ++a) {
         Geom geo;
         if (g->d == 2) col_dispatch<T, 2>(g->logn[a], OP_QUERY, nullptr, nullptr, &geo);
@@ -151,8 +164,7 @@ int ensure_workspace(lsfft_grid* g, int prec, int st, int max_iter) {
         g->ws_prec = prec;
         g->ws_st = st;
     }
-    const int nb = row_blocks(g, prec);
-    const int64_t need = (int64_t)nb * (4 * g->d + 1);
+    const int64_t need = (int64_t)g->sm_count * 32 * (4 * g->d + 1);   // >= any persistent row grid
     if (need > g->partials_cap) {
         clear_graphs(g);
         cudaFree(g->partials);
@@ -255,8 +267,10 @@ int create_common(int d, const int64_t n[3], const uint8_t* mask, bool on_device
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->mask, mask, (size_t)g->N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                             g->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&g->prm_dev, sizeof(SchemeParams));
-    if (e == cudaSuccess) e = cudaMallocHost(&g->prm_host, sizeof(SchemeParams));
+    if (e == cudaSuccess) {
+        g->prm_host = new (std::nothrow) SchemeParams();
+        if (!g->prm_host) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&g->ctrl_dev, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost(&g->ctrl_host, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
@@ -363,6 +377,56 @@ std::string build_params(const lsfft_grid* g, cplx s1, const double* e, const ls
 }
 
 template <typename T>
+cx<T> kc(const double (&v)[2], double scale = 1.0) {
+    cx<T> r;
+    r.x = (T)(v[0] * scale);
+    r.y = (T)(v[1] * scale);
+    return r;
+}
+
+// Scheme constants rounded to the field precision for the kernels.
+template <typename T>
+KConst<T> make_kconst(const SchemeParams& P) {
+    KConst<T> K;
+    memset(&K, 0, sizeof(K));
+    K.a_in = kc<T>(P.a_in);
+    K.a_out = kc<T>(P.a_out);
+    K.k1 = kc<T>(P.k1);
+    K.k2 = kc<T>(P.k2);
+    K.k3 = kc<T>(P.k3);
+    K.tm1p1 = kc<T>(P.tm1p1);
+    K.p1 = kc<T>(P.p1);
+    K.p2 = kc<T>(P.p2);
+    K.p3 = kc<T>(P.p3);
+    K.w = kc<T>(P.w);
+    K.inv2s0 = kc<T>(P.inv2s0);
+    K.s1 = kc<T>(P.sigma1);
+    K.g_a = kc<T>(P.g_a, P.inv_ntot);
+    K.g_b = kc<T>(P.g_b, P.inv_ntot);
+    K.g_a0 = kc<T>(P.g_a0, P.inv_ntot);
+    K.g_ce = kc<T>(P.g_ce);
+    for (int c = 0; c < 3; ++c) K.e[c] = (T)P.e[c];
+    K.scheme = P.scheme;
+    K.green = P.green;
+    return K;
+}
+
+// The packed real layout applies in 2-D when every coefficient the scheme
+// multiplies real fields by is real (p_2, p_3 and what they scale are purely
+// imaginary): then Q, J and E stay real and S, T purely imaginary.
+bool packed_layout(const lsfft_grid* g, const SchemeParams& P) {
+    if (g->d != 2) return false;
+    const double* re_only[] = {P.sigma1, P.a_in, P.a_out, P.k1, P.k2, P.tm1p1, P.p1, P.w, P.inv2s0,
+                               P.g_a, P.g_b, P.g_a0, P.g_ce, P.iq_in, P.iq_out};
+    for (const double* v : re_only)
+        if (v[1] != 0.0) return false;
+    const double* im_only[] = {P.p2, P.p3, P.k3, P.is_in, P.it_in};
+    for (const double* v : im_only)
+        if (v[0] != 0.0) return false;
+    return true;
+}
+
+template <typename T>
 PassArgs<T> base_args(lsfft_grid* g, int st) {
     PassArgs<T> A;
     memset(&A, 0, sizeof(A));
@@ -371,7 +435,8 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
     A.S = st >= 1 ? (cx<T>*)g->S : nullptr;
     A.Tf = st >= 2 ? (cx<T>*)g->T : nullptr;
     A.mask = g->mask;
-    A.prm = g->prm_dev;
+    A.packed = g->packed;
+    A.k = make_kconst<T>(*g->prm_host);
     A.ctrl = g->ctrl_dev;
     A.partials = g->partials;
     for (int a = 0; a < 3; ++a) A.fd[a] = a < g->d ? (const cx<T>*)g->fd[a][p] : nullptr;
@@ -387,8 +452,21 @@ cudaError_t launch_row(lsfft_grid* g, int st, int mode, cx<T>* Eout) {
     A.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[0] : nullptr;
     A.n_lines = g->N / g->n[0];
     A.mode = mode;
+    A.grid_blocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
     if (g->d == 2) return row_dispatch<T, 2>(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
     return row_dispatch<T, 3>(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
+}
+
+template <typename T>
+cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
+    Geom geo;
+    if (g->d == 2) col_dispatch<T, 2>(g->logn[axis], OP_QUERY, nullptr, nullptr, &geo);
+    else col_dispatch<T, 3>(g->logn[axis], OP_QUERY, nullptr, nullptr, &geo);
+    const int64_t items = A->packed ? (g->n[0] / 2 + geo.per_block) / geo.per_block   // Hermitian column pairs
+                                    : (A->n_inner / geo.per_block) * A->n_outer;
+    A->grid_blocks = (int)persistent_blocks(g, items, geo.blocks_per_sm);
+    if (g->d == 2) return col_dispatch<T, 2>(g->logn[axis], OP_LAUNCH, A, g->stream, nullptr);
+    return col_dispatch<T, 3>(g->logn[axis], OP_LAUNCH, A, g->stream, nullptr);
 }
 
 template <typename T>
@@ -402,7 +480,7 @@ cudaError_t launch_cols(lsfft_grid* g, int st) {
         A.n_outer = 1;
         A.line_axis = 1;
         A.mode = MODE_COL_GAMMA;
-        return col_dispatch<T, 2>(g->logn[1], OP_LAUNCH, &A, g->stream, nullptr);
+        return col_launch<T>(g, 1, &A);
     }
     PassArgs<T> Y = A;
     Y.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[1] : nullptr;
@@ -412,7 +490,7 @@ cudaError_t launch_cols(lsfft_grid* g, int st) {
     Y.n_outer = g->n[2];
     Y.line_axis = 1;
     Y.mode = MODE_COL_FWD;
-    cudaError_t e = col_dispatch<T, 3>(g->logn[1], OP_LAUNCH, &Y, g->stream, nullptr);
+    cudaError_t e = col_launch<T>(g, 1, &Y);
     if (e != cudaSuccess) return e;
     PassArgs<T> Z = A;
     Z.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[2] : nullptr;
@@ -422,36 +500,50 @@ cudaError_t launch_cols(lsfft_grid* g, int st) {
     Z.n_outer = 1;
     Z.line_axis = 2;
     Z.mode = MODE_COL_GAMMA;
-    e = col_dispatch<T, 3>(g->logn[2], OP_LAUNCH, &Z, g->stream, nullptr);
+    e = col_launch<T>(g, 2, &Z);
     if (e != cudaSuccess) return e;
     Y.mode = MODE_COL_INV;
-    return col_dispatch<T, 3>(g->logn[1], OP_LAUNCH, &Y, g->stream, nullptr);
+    return col_launch<T>(g, 1, &Y);
 }
 
 template <typename T>
 cudaError_t launch_iteration(lsfft_grid* g, int st, int nblocks, int row_mode) {
     cudaError_t e = launch_row<T>(g, st, row_mode, nullptr);
     if (e != cudaSuccess) return e;
-    e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, g->prm_dev, g->ctrl_dev, g->hist, 0, g->stream);
+    e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 0, g->stream);
     if (e != cudaSuccess) return e;
     return launch_cols<T>(g, st);
 }
 
+// The iteration graph bakes the scheme constants into its kernel parameters, so
+// it is captured anew for every solve and, when a graph of the same shape is
+// cached, applied to it with cudaGraphExecUpdate (cheap) instead of a fresh
+// instantiation.
 template <typename T>
 int get_graph(lsfft_grid* g, int st, int nblocks, int check_every, cudaGraphExec_t* out) {
     const GraphKey key{(int)sizeof(T), st, check_every};
-    auto it = g->graphs.find(key);
-    if (it != g->graphs.end()) {
-        *out = it->second;
-        return LSFFT_OK;
-    }
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < check_every && le == cudaSuccess; ++i) le = launch_iteration<T>(g, st, nblocks, MODE_ROW_ITER);
     cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
-    if (le != cudaSuccess) return fail_cuda(le, "graph capture launch");
+    if (le != cudaSuccess) {
+        if (ce == cudaSuccess) cudaGraphDestroy(graph);
+        return fail_cuda(le, "graph capture launch");
+    }
     if (ce != cudaSuccess) return fail_cuda(ce, "cudaStreamEndCapture");
+    auto it = g->graphs.find(key);
+    if (it != g->graphs.end()) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(it->second, graph, &info) == cudaSuccess) {
+            cudaGraphDestroy(graph);
+            *out = it->second;
+            return LSFFT_OK;
+        }
+        cudaGetLastError();
+        cudaGraphExecDestroy(it->second);
+        g->graphs.erase(it);
+    }
     cudaGraphExec_t exec;
     cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -477,20 +569,19 @@ int start_solve(lsfft_grid* g, int st) {
     int rc0 = ensure_prepared<T>(g);
     if (rc0 != LSFFT_OK) return rc0;
     const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
-    CK(cudaMemcpyAsync(g->prm_dev, g->prm_host, sizeof(SchemeParams), cudaMemcpyHostToDevice, g->stream));
     CK(cudaMemsetAsync(g->ctrl_dev, 0, sizeof(Ctrl), g->stream));
     CK(cudaEventRecord(g->ev0, g->stream));
     CK(launch_init<T>((cx<T>*)g->X, st >= 1 ? (cx<T>*)g->S : nullptr, st >= 2 ? (cx<T>*)g->T : nullptr, g->mask,
-                      g->prm_dev, g->N, g->d, g->sm_count, g->stream));
+                      *g->prm_host, g->N, g->d, g->packed, g->sm_count, g->stream));
     CK(launch_iteration<T>(g, st, nblocks, MODE_ROW_FIRST));
     return LSFFT_OK;
 }
 
 template <typename T>
 int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
-    const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
     int rc = ensure_prepared<T>(g);   // shared-memory limits must be set before capture
     if (rc != LSFFT_OK) return rc;
+    const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
     cudaGraphExec_t exec;
     rc = get_graph<T>(g, st, nblocks, o->check_every, &exec);
     if (rc != LSFFT_OK) return rc;
@@ -519,7 +610,7 @@ int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     CK(cudaMallocAsync(&E, ebytes, g->stream));
     cudaError_t e = launch_row<T>(g, st, MODE_ROW_OUTPUT, (cx<T>*)E);
     if (e == cudaSuccess)
-        e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, g->prm_dev, g->ctrl_dev, g->hist, 1, g->stream);
+        e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1, g->stream);
     if (e == cudaSuccess) e = cudaEventRecord(g->ev1, g->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -544,6 +635,7 @@ int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     cudaEventElapsedTime(&ms, g->ev0, g->ev1);
     res->solve_ms = ms;
     res->kernel_launches = kernels;
+    res->packed = g->packed;
     const int L = res->hist_len;
     double* h = (double*)malloc(sizeof(double) * HIST_STRIDE * L);
     res->hist_sigma_re = (double*)malloc(sizeof(double) * L);
@@ -607,9 +699,8 @@ void lsfft_destroy_grid(lsfft_grid* g) {
     cudaFree(g->T);
     cudaFree(g->partials);
     cudaFree(g->hist);
-    cudaFree(g->prm_dev);
     cudaFree(g->ctrl_dev);
-    if (g->prm_host) cudaFreeHost(g->prm_host);
+    delete g->prm_host;
     if (g->ctrl_host) cudaFreeHost(g->ctrl_host);
     for (int a = 0; a < 3; ++a) {
         cudaFree(g->tw[a]);
@@ -668,7 +759,7 @@ int check_and_setup(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsf
     }
     const bool fp32 = o->precision == LSFFT_FP32;
     if (!(fp32 ? col_supported<float>(g) : col_supported<double>(g))) {
-        g_last_error = "grid size not supported in this precision (FP64 2-D lines up to 4096)";
+        g_last_error = "grid size not supported in this precision (FP64: line lengths up to 4096)";
         return LSFFT_EINVAL;
     }
     std::string why = build_params(g, s1, e, o, g->prm_host);
@@ -678,6 +769,7 @@ int check_and_setup(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsf
     }
     const int st = o->scheme == LSFFT_EM_SUB ? 2 : (o->scheme == LSFFT_MS_SUB ? 1 : 0);
     *st_out = st;
+    g->packed = packed_layout(g, *g->prm_host) ? 1 : 0;
     g->bench_prec = -1;
     return ensure_workspace(g, o->precision, st, o->max_iter);
 }

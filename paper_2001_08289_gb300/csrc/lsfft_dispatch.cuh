@@ -12,24 +12,35 @@ namespace lsfft {
 
 template <typename T, int N, int D>
 cudaError_t row_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
-    using Cfg = RowCfg<T, N>;
-    if (op == OP_QUERY) {
-        g->threads = Cfg::THREADS;
-        g->per_block = Cfg::LPB;
-        g->smem = Cfg::SMEM;
-        g->supported = true;
-        return cudaSuccess;
+    using Cfg = RowCfg<T, N, D>;
+    static int bps = 0;   // resident blocks per SM, set by OP_PREPARE
+    if constexpr (!Cfg::SUPPORTED) {
+        if (op == OP_QUERY) g->supported = false;
+        return op == OP_QUERY ? cudaSuccess : cudaErrorInvalidValue;
+    } else {
+        if (op == OP_QUERY) {
+            g->threads = Cfg::THREADS;
+            g->per_block = Cfg::LPB;
+            g->smem = Cfg::SMEM;
+            g->blocks_per_sm = bps;
+            g->supported = true;
+            return cudaSuccess;
+        }
+        if (op == OP_PREPARE) {
+            cudaError_t e = cudaFuncSetAttribute(row_pass<T, N, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 Cfg::SMEM);
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, row_pass<T, N, D>, Cfg::THREADS, Cfg::SMEM);
+        }
+        row_pass<T, N, D><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
+        return cudaGetLastError();
     }
-    if (op == OP_PREPARE)
-        return cudaFuncSetAttribute(row_pass<T, N, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    const int64_t blocks = (A->n_lines + Cfg::LPB - 1) / Cfg::LPB;
-    row_pass<T, N, D><<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
-    return cudaGetLastError();
 }
 
 template <typename T, int N, int D>
 cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
     using Cfg = ColCfg<T, N, D>;
+    static int bps = 0;
     if constexpr (!Cfg::SUPPORTED) {
         if (op == OP_QUERY) g->supported = false;
         return op == OP_QUERY ? cudaSuccess : cudaErrorInvalidValue;
@@ -38,13 +49,17 @@ cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
             g->threads = Cfg::THREADS;
             g->per_block = Cfg::COLS;
             g->smem = Cfg::SMEM;
+            g->blocks_per_sm = bps;
             g->supported = true;
             return cudaSuccess;
         }
-        if (op == OP_PREPARE)
-            return cudaFuncSetAttribute(col_pass<T, N, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-        const int64_t blocks = (A->n_inner / Cfg::COLS) * A->n_outer;
-        col_pass<T, N, D><<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
+        if (op == OP_PREPARE) {
+            cudaError_t e = cudaFuncSetAttribute(col_pass<T, N, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 Cfg::SMEM);
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass<T, N, D>, Cfg::THREADS, Cfg::SMEM);
+        }
+        col_pass<T, N, D><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
         return cudaGetLastError();
     }
 }

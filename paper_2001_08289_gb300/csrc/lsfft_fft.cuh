@@ -123,14 +123,28 @@ struct LineFFT {
     __device__ __forceinline__ static void twiddle(C (&a)[R], int jm, int span, const C* __restrict__ tw) {
         // a[r] *= W_span^{jm r}, forward W = exp(-2 pi i / span)
         if constexpr (sizeof(T) == 4) {
+            // W^(jm r) from the bases W^(jm), W^(2 jm), W^(4 jm), W^(8 jm): each power is a
+            // product of at most four bases (a few ulp), formed when needed so that no
+            // table of R twiddles stays live in registers.
             float s, c;
             sincospif(2.0f * (float)jm / (float)span, &s, &c);
-            C w[R];
-            w[1] = mkc(c, INV ? s : -s);
+            C b[4];
+            b[0] = mkc(c, INV ? s : -s);
 #pragma unroll
-            for (int r = 2; r < R; ++r) w[r] = cmul(w[r / 2], w[r - r / 2]);
+            for (int i = 1; i < 4; ++i) b[i] = cmul(b[i - 1], b[i - 1]);
 #pragma unroll
-            for (int r = 1; r < R; ++r) a[r] = cmul(a[r], w[r]);
+            for (int r = 1; r < R; ++r) {
+                C w = mkc(1.0f, 0.0f);
+                bool first = true;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (r & (1 << i)) {
+                        w = first ? b[i] : cmul(w, b[i]);
+                        first = false;
+                    }
+                }
+                a[r] = cmul(a[r], w);
+            }
         } else {
             const int step = (N / span) * jm;
 #pragma unroll

@@ -7,11 +7,26 @@
 // the extra components of H'' (Eq. J27, J36), live in real space and are
 // touched only on phase-1 voxels (they vanish on phase 2).
 //
+// Packed real layout (2-D, every scheme coefficient real, i.e. real sigma_1 and
+// a real reference medium): the fields are real (S and T purely imaginary), so
+// the two components travel as one complex plane Z = F_x + i F_y (S and T as
+// s_x + i s_y with S = i s), halving bytes and transforms.  The strided pass
+// then splits the spectra with the Hermitian pairing of k and -k.
+//
 // One iteration (2-D): row pass [inverse x-DFT -> pointwise scheme update and
 // volume averages -> forward x-DFT], finalize (FP64 sums, sigma_k, stop rule),
 // strided pass over y [forward y-DFT -> Gamma multiply per frequency -> inverse
 // y-DFT].  3-D: row pass, finalize, y forward, z [forward, Gamma, inverse],
 // y inverse.  Every pass is in place.
+//
+// Both passes are persistent: a block owns a stream of work items (a few rows,
+// or a few line starts of the strided axis).  The lines of an item are staged
+// in shared memory by cp.async, one commit group per line; a thread transforms
+// one line at a time in registers (positions t + TL*m) and parks the result
+// back in the stage buffer at its own positions, so the pointwise update and
+// the Gamma multiply read all lines without extra barriers.  As soon as the
+// last pass over a staged line has read it, the copy of the next item's line
+// is issued, so loads overlap the remaining transforms of the current item.
 #pragma once
 
 #include "lsfft_fft.cuh"
@@ -19,41 +34,87 @@
 
 namespace lsfft {
 
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int roundup16(int v) { return (v + 15) / 16 * 16; }
+
+// Line pitches: the stage buffer keeps lines dense (cp.async destinations,
+// 16-byte aligned); the exchange buffer is padded one slot per 16 elements.
+// When fewer than 16 threads share a line, consecutive line groups are offset
+// by TL slots so that the groups of one warp fall into different banks.
+template <typename T, int N, int TL>
+struct Pitch {
+    static constexpr int GPAD = TL < 16 ? cmax(TL, 2) : 0;
+    static constexpr int S = N + GPAD;
+    static constexpr int X = roundup16(N + N / 16) + GPAD;
+};
+
 // ---------------------------------------------------------------------------
-// Launch geometry, shared by the kernels and the host dispatch.
+// Launch geometry, shared by the kernels and the host dispatch.  MINB is the
+// number of blocks per SM the shared-memory footprint allows (at most 4); it is
+// passed to __launch_bounds__ so that registers do not become the tighter limit.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+__host__ __device__ constexpr int min_blocks(int smem, int threads) {
+    return cmax(1, cmin(cmin(4, (227 * 1024) / (smem + 1024)), 2048 / threads));
+}
+
+template <typename T, int N, int D>
 struct RowCfg {
-    static constexpr int E0 = sizeof(T) == 4 ? 16 : 8;
-    static constexpr int E = (N < E0) ? N : ((N / 512 > E0) ? N / 512 : E0);
+    static constexpr int CS = (int)sizeof(cx<T>);
+    static constexpr int E = sizeof(T) == 4 ? (N < 16 ? N : 16) : (N < 8 ? N : 8);
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
     static constexpr int TL = N / E;
-    static constexpr int LPB = (256 / TL) > 0 ? (256 / TL) : 1;      // rows per block
+    static constexpr int LPB = cmax(1, 256 / TL);                 // rows per item
     static constexpr int THREADS = LPB * TL;
-    static constexpr int SMEM = LPB * LinePad<N>::size * (int)sizeof(cx<T>);
+    using P = Pitch<T, N, TL>;
+    static constexpr int S_BYTES = D * LPB * P::S * CS;
+    static constexpr int X_BYTES = LPB * P::X * CS;
+    static constexpr int M_BYTES = roundup16(LPB * N);
+    static constexpr int SMEM = S_BYTES + X_BYTES + M_BYTES;
+    static constexpr bool SUPPORTED = SMEM <= 227 * 1024 && THREADS <= 1024;
+    static constexpr int MINB = min_blocks(SMEM, THREADS);
 };
 
 template <typename T, int N, int D>
 struct ColCfg {
     static constexpr int CS = (int)sizeof(cx<T>);
-    static constexpr int E0 = sizeof(T) == 4 ? 16 : 8;
-    static constexpr int EMAX = sizeof(T) == 4 ? 32 : 16;
-    static constexpr int COLMAX = sizeof(T) == 4 ? 4 : 2;    // 32-byte sectors
+    static constexpr int E = sizeof(T) == 4 ? (N < 16 ? N : 16) : (N < 8 ? N : 8);
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
-    static constexpr int e_for(int cols) {
-        return (N < E0) ? N : ((cols * D * N / 512 > E0) ? cols * D * N / 512 : E0);
-    }
-    static constexpr bool ok(int cols) {
-        return e_for(cols) <= EMAX && cols * D * LinePad<N>::size * CS <= 200 * 1024;
-    }
-    static constexpr int COLS = ok(COLMAX) ? COLMAX : (ok(COLMAX / 2) ? COLMAX / 2 : 1);
-    static constexpr int E = e_for(COLS);
     static constexpr int TL = N / E;
-    static constexpr int G = COLS * D;                 // line groups per block
-    static constexpr int THREADS = G * TL;
-    static constexpr int SMEM = G * LinePad<N>::size * CS;
-    static constexpr bool SUPPORTED = ok(COLS) && THREADS <= 1024;
+    static constexpr int L = D > 2 ? D : 2;                       // staged lines per group
+    using P = Pitch<T, N, TL>;
+    static constexpr int bytes(int cols) { return cols * (L * P::S + P::X) * CS; }
+    static constexpr int CMAX = sizeof(T) == 4 ? 4 : 2;           // 32-byte sectors per row
+    static constexpr int fit(int cols) {
+        return cols == 0 ? 0 : ((bytes(cols) <= 110 * 1024 && cols * TL <= 512) ? cols : fit(cols / 2));
+    }
+    static constexpr int COLS = cmax(1, fit(CMAX));
+    static constexpr int THREADS = COLS * TL;
+    static constexpr int S_BYTES = COLS * L * P::S * CS;
+    static constexpr int SMEM = bytes(COLS);
+    static constexpr bool SUPPORTED = SMEM <= 227 * 1024 && THREADS <= 1024;
+    static constexpr int MINB = min_blocks(SMEM, THREADS);
 };
+
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, valid on sm_103a).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// Wait until at most `n` (0..2) of this thread's most recent groups are pending.
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+    if (n <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Reductions: thread-local FP64 -> warp shuffle -> block -> partials[block][NV]
@@ -82,6 +143,20 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], double* __
     }
 }
 
+// Scheme constants rounded to the field precision, passed by value as a
+// kernel parameter (they sit in the constant bank and feed the FMAs directly).
+template <typename T>
+struct KConst {
+    cx<T> a_in, a_out;          // MS: sigma/sigma_0 - 1 per phase; EM: W per phase
+    cx<T> k1, k2, k3, tm1p1;    // MS in H''
+    cx<T> p1, p2, p3, w;        // EM in H''
+    cx<T> inv2s0, s1;
+    cx<T> g_a, g_b, g_a0;       // Gamma step coefficients, already divided by N
+    cx<T> g_ce;                 // zero-mode source coefficient
+    T e[3];
+    int scheme, green;
+};
+
 // ---------------------------------------------------------------------------
 // Pointwise scheme update on one voxel (all d components).
 //   q[c]   : Q component (real space) on entry; on exit the field handed to the
@@ -90,124 +165,156 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], double* __
 //   E, J   : the physical fields of the current iterate, for the averages.
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-struct Pointwise {
+__device__ __forceinline__ void pointwise(const KConst<T>& K, cx<T> (&q)[D], bool inc, cx<T>* __restrict__ Sv,
+                                          cx<T>* __restrict__ Tv, int64_t cs, cx<T> (&E)[D], cx<T> (&J)[D],
+                                          bool write_st) {
     using C = cx<T>;
-    C a_in, a_out, k1, k2, k3, p1, p2, p3, w, inv2s0, tm1p1, half;
-    C s1;
-    int scheme;
-
-    __device__ __forceinline__ void load(const SchemeParams& P) {
-        scheme = P.scheme;
-        a_in = mkc((T)P.a_in[0], (T)P.a_in[1]);
-        a_out = mkc((T)P.a_out[0], (T)P.a_out[1]);
-        k1 = mkc((T)P.k1[0], (T)P.k1[1]);
-        k2 = mkc((T)P.k2[0], (T)P.k2[1]);
-        k3 = mkc((T)P.k3[0], (T)P.k3[1]);
-        p1 = mkc((T)P.p1[0], (T)P.p1[1]);
-        p2 = mkc((T)P.p2[0], (T)P.p2[1]);
-        p3 = mkc((T)P.p3[0], (T)P.p3[1]);
-        w = mkc((T)P.w[0], (T)P.w[1]);
-        inv2s0 = mkc((T)P.inv2s0[0], (T)P.inv2s0[1]);
-        tm1p1 = mkc((T)P.tm1p1[0], (T)P.tm1p1[1]);
-        s1 = mkc((T)P.sigma1[0], (T)P.sigma1[1]);
-    }
-
-    // S/T pointers already offset to this voxel; comp stride cs.
-    __device__ __forceinline__ void apply(C (&q)[D], bool inc, C* __restrict__ Sv, C* __restrict__ Tv,
-                                          int64_t cs, C (&E)[D], C (&J)[D], bool write_st) const {
-        if (scheme == SCHEME_MS) {
-            const C a = inc ? a_in : a_out;
+    if (K.scheme == SCHEME_MS) {            // Eq. J0-0: tau = (sigma/sigma_0 - 1) E
+        const C a = inc ? K.a_in : K.a_out;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            E[c] = q[c];
+            J[c] = inc ? cmul(K.s1, q[c]) : q[c];
+            q[c] = cmul(a, q[c]);
+        }
+    } else if (K.scheme == SCHEME_EM) {     // W P with W = (sigma - sigma_0)/(sigma + sigma_0)
+        const C W = inc ? K.a_in : K.a_out;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const C wp = cmul(W, q[c]);
+            E[c] = cmul(csub(q[c], wp), K.inv2s0);
+            J[c] = cscale(cadd(q[c], wp), (T)0.5);
+            q[c] = wp;
+        }
+    } else if (K.scheme == SCHEME_MS_SUB) { // Eq. J36, J42a: tau'' = (L''/sigma_0'' - 1) E''
+        if (inc) {
+            C s[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) s[c] = Sv[c * cs];
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const C cc = cadd(cmul(K.p1, q[c]), cmul(K.p2, s[c]));
+                E[c] = q[c];
+                J[c] = cadd(q[c], cmul(K.tm1p1, cc));
+                const C tq = cadd(cmul(K.k1, cc), cmul(K.k2, q[c]));
+                const C ts = cadd(cmul(K.k3, cc), cmul(K.k2, s[c]));
+                q[c] = tq;
+                s[c] = cneg(ts);
+            }
+            if (write_st) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) Sv[c * cs] = s[c];
+            }
+        } else {
 #pragma unroll
             for (int c = 0; c < D; ++c) {
                 E[c] = q[c];
-                J[c] = inc ? cmul(s1, q[c]) : q[c];
-                q[c] = cmul(a, q[c]);
+                J[c] = q[c];
+                q[c] = cmul(K.k2, q[c]);
             }
-        } else if (scheme == SCHEME_EM) {
-            const C W = inc ? a_in : a_out;
+        }
+    } else {                                // Eq. J36, J43: W'' = w (I - 2 p p^T) on phase 1
+        if (inc) {
+            C s[D], tt[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                const C wp = cmul(W, q[c]);
-                E[c] = cmul(csub(q[c], wp), inv2s0);
-                J[c] = cscale(cadd(q[c], wp), (T)0.5);
-                q[c] = wp;
+                s[c] = Sv[c * cs];
+                tt[c] = Tv[c * cs];
             }
-        } else if (scheme == SCHEME_MS_SUB) {
-            if (inc) {
-                C s[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) s[c] = Sv[c * cs];
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const C cc = cadd(cmul(p1, q[c]), cmul(p2, s[c]));
-                    E[c] = q[c];
-                    J[c] = cadd(q[c], cmul(tm1p1, cc));
-                    const C tq = cadd(cmul(k1, cc), cmul(k2, q[c]));
-                    const C ts = cadd(cmul(k3, cc), cmul(k2, s[c]));
-                    q[c] = tq;
-                    s[c] = cneg(ts);
-                }
-                if (write_st) {
-#pragma unroll
-                    for (int c = 0; c < D; ++c) Sv[c * cs] = s[c];
-                }
-            } else {
+            for (int c = 0; c < D; ++c) {
+                const C cc = cadd(cadd(cmul(K.p1, q[c]), cmul(K.p2, s[c])), cmul(K.p3, tt[c]));
+                const C cc2 = cadd(cc, cc);
+                const C wq = cmul(K.w, csub(q[c], cmul(K.p1, cc2)));
+                const C ws = cmul(K.w, csub(s[c], cmul(K.p2, cc2)));
+                const C wt = cmul(K.w, csub(tt[c], cmul(K.p3, cc2)));
+                E[c] = cmul(csub(q[c], wq), K.inv2s0);
+                J[c] = cscale(cadd(q[c], wq), (T)0.5);
+                q[c] = wq;
+                s[c] = cneg(ws);
+                tt[c] = wt;
+            }
+            if (write_st) {
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    E[c] = q[c];
-                    J[c] = q[c];
-                    q[c] = cmul(k2, q[c]);
+                    Sv[c * cs] = s[c];
+                    Tv[c * cs] = tt[c];
                 }
             }
-        } else {   // SCHEME_EM_SUB
-            if (inc) {
-                C s[D], tt[D];
+        } else {
 #pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    s[c] = Sv[c * cs];
-                    tt[c] = Tv[c * cs];
-                }
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const C cc = cadd(cadd(cmul(p1, q[c]), cmul(p2, s[c])), cmul(p3, tt[c]));
-                    const C cc2 = cadd(cc, cc);
-                    const C wq = cmul(w, csub(q[c], cmul(p1, cc2)));
-                    const C ws = cmul(w, csub(s[c], cmul(p2, cc2)));
-                    const C wt = cmul(w, csub(tt[c], cmul(p3, cc2)));
-                    E[c] = cmul(csub(q[c], wq), inv2s0);
-                    J[c] = cscale(cadd(q[c], wq), (T)0.5);
-                    q[c] = wq;
-                    s[c] = cneg(ws);
-                    tt[c] = wt;
-                }
-                if (write_st) {
-#pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        Sv[c * cs] = s[c];
-                        Tv[c * cs] = tt[c];
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < D; ++c) {
-                    const C wq = cmul(w, q[c]);
-                    E[c] = cmul(csub(q[c], wq), inv2s0);
-                    J[c] = cscale(cadd(q[c], wq), (T)0.5);
-                    q[c] = wq;
-                }
+            for (int c = 0; c < D; ++c) {
+                const C wq = cmul(K.w, q[c]);
+                E[c] = cmul(csub(q[c], wq), K.inv2s0);
+                J[c] = cscale(cadd(q[c], wq), (T)0.5);
+                q[c] = wq;
             }
         }
     }
-};
+}
+
+// The same update in the packed real layout: z = Q_x + i Q_y and, on phase 1,
+// s = s_x + i s_y, tau = tau_x + i tau_y with S = i s, T = i tau.  Every
+// coefficient is real here; with p_2 = i q_2 and p_3 = i q_3 one has
+// p . (Q, S, T) = p_1 Q - q_2 s - q_3 tau componentwise.
+template <typename T>
+__device__ __forceinline__ void pointwise_packed(const KConst<T>& K, cx<T>& z, bool inc, cx<T>* __restrict__ Sv,
+                                                 cx<T>* __restrict__ Tv, cx<T>& E, cx<T>& J, bool write_st) {
+    using C = cx<T>;
+    if (K.scheme == SCHEME_MS) {
+        E = z;
+        J = inc ? cscale(z, K.s1.x) : z;
+        z = cscale(z, inc ? K.a_in.x : K.a_out.x);
+    } else if (K.scheme == SCHEME_EM) {
+        const C wp = cscale(z, inc ? K.a_in.x : K.a_out.x);
+        E = cscale(csub(z, wp), K.inv2s0.x);
+        J = cscale(cadd(z, wp), (T)0.5);
+        z = wp;
+    } else if (K.scheme == SCHEME_MS_SUB) {
+        if (inc) {
+            const C s = *Sv;
+            const C cc = csub(cscale(z, K.p1.x), cscale(s, K.p2.y));
+            E = z;
+            J = cadd(z, cscale(cc, K.tm1p1.x));
+            const C sn = cneg(cadd(cscale(cc, K.k3.y), cscale(s, K.k2.x)));
+            z = cadd(cscale(cc, K.k1.x), cscale(z, K.k2.x));
+            if (write_st) *Sv = sn;
+        } else {
+            E = z;
+            J = z;
+            z = cscale(z, K.k2.x);
+        }
+    } else {
+        if (inc) {
+            const C s = *Sv, tt = *Tv;
+            const C cc = csub(csub(cscale(z, K.p1.x), cscale(s, K.p2.y)), cscale(tt, K.p3.y));
+            const C cc2 = cadd(cc, cc);
+            const C wq = cscale(csub(z, cscale(cc2, K.p1.x)), K.w.x);
+            const C sn = cscale(csub(s, cscale(cc2, K.p2.y)), -K.w.x);
+            const C tn = cscale(csub(tt, cscale(cc2, K.p3.y)), K.w.x);
+            E = cscale(csub(z, wq), K.inv2s0.x);
+            J = cscale(cadd(z, wq), (T)0.5);
+            z = wq;
+            if (write_st) {
+                *Sv = sn;
+                *Tv = tn;
+            }
+        } else {
+            const C wq = cscale(z, K.w.x);
+            E = cscale(csub(z, wq), K.inv2s0.x);
+            J = cscale(cadd(z, wq), (T)0.5);
+            z = wq;
+        }
+    }
+}
 
 template <typename T>
 struct PassArgs {
-    cx<T>* X;                 // state, [D][Ntot]
+    cx<T>* X;                 // state, [D][Ntot] (packed: plane 0 only)
     cx<T>* S;                 // H'' S component, [D][Ntot] (or null)
     cx<T>* Tf;                // H'' T component, [D][Ntot] (or null)
     cx<T>* Eout;              // output field, [D][Ntot] (row pass, output mode)
     const uint8_t* mask;      // [Ntot]
-    const SchemeParams* prm;
     Ctrl* ctrl;
     double* partials;         // [gridDim.x][NV]
     const cx<T>* tw;          // FP64 twiddle table W_N^k of the pass's line length
@@ -221,116 +328,181 @@ struct PassArgs {
     int n[3];                 // grid extents (x, y, z)
     int line_axis;            // strided pass: 1 (y) or 2 (z)
     int mode;                 // PassMode
+    int grid_blocks;          // persistent grid size chosen by the host
+    int packed;               // packed real layout (2-D only)
+    KConst<T> k;
 };
 
 // ---------------------------------------------------------------------------
-// Row pass: lines along x (contiguous).
+// Row pass: lines along x (contiguous).  Work item = LPB consecutive rows.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int D>
-__global__ void __launch_bounds__(RowCfg<T, N>::THREADS)
+__global__ void __launch_bounds__(RowCfg<T, N, D>::THREADS, RowCfg<T, N, D>::MINB)
 row_pass(const PassArgs<T> A) {
-    using Cfg = RowCfg<T, N>;
+    using Cfg = RowCfg<T, N, D>;
     using C = cx<T>;
-    constexpr int E = Cfg::E, TL = Cfg::TL, NV = 4 * D + 1;
+    constexpr int E = Cfg::E, TL = Cfg::TL, LPB = Cfg::LPB, NV = 4 * D + 1;
+    constexpr int PS = Cfg::P::S, PX = Cfg::P::X;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int mode = A.mode;
     if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;
 
+    C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][LPB][PS]
     const int g = threadIdx.x / TL, t = threadIdx.x % TL;
-    C* sm = reinterpret_cast<C*>(smem_raw) + g * LinePad<N>::size;
-    const int64_t row = (int64_t)blockIdx.x * Cfg::LPB + g;
-    const bool active = row < A.n_lines;
-    const int64_t base = row * N;
+    C* Xb = reinterpret_cast<C*>(smem_raw + Cfg::S_BYTES) + g * PX;            // exchange line
+    uint8_t* Mb = smem_raw + Cfg::S_BYTES + Cfg::X_BYTES;                      // [LPB][N]
+    const int64_t n_items = (A.n_lines + LPB - 1) / LPB;
+    const int L = A.packed ? 1 : D;
 
-    Pointwise<T, D> pw;
-    pw.load(*A.prm);
-
-    C v[D][E];
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int m = 0; m < E; ++m)
-            v[c][m] = active ? A.X[c * A.Ntot + base + t + TL * m] : mkc((T)0, (T)0);
-
-    if (mode != MODE_ROW_FIRST) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) LineFFT<T, N, E, Cfg::RMAX, true>::run(v[c], sm, t, A.tw);
-    }
+    // Stage line l of the rows of `item` (and the mask with line 0): one commit group.
+    auto prefetch_line = [&](int64_t item, int l) {
+        constexpr int CH = N * (int)sizeof(C) / 16;          // 16-byte chunks per line
+        for (int i = threadIdx.x; i < LPB * CH; i += Cfg::THREADS) {
+            const int ch = i % CH, r = i / CH;
+            const int64_t row = item * LPB + r;
+            if (row < A.n_lines)
+                cp_async16(reinterpret_cast<unsigned char*>(Sb + (l * LPB + r) * PS) + 16 * ch,
+                           reinterpret_cast<const unsigned char*>(A.X + l * A.Ntot + row * N) + 16 * ch);
+        }
+        if (l == 0) {
+            constexpr int MCH = N / 16;
+            for (int i = threadIdx.x; i < LPB * MCH; i += Cfg::THREADS) {
+                const int ch = i % MCH, r = i / MCH;
+                const int64_t row = item * LPB + r;
+                if (row < A.n_lines) cp_async16(Mb + r * N + 16 * ch, A.mask + row * N + 16 * ch);
+            }
+        }
+        cp_async_commit();
+    };
 
     double acc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    if (active) {
-        T sE[D][2], sJ[D][2], sE2 = 0;
+
+    int64_t item = blockIdx.x;
+    if (item < n_items)
+        for (int l = 0; l < L; ++l) prefetch_line(item, l);
+    for (; item < n_items; item += A.grid_blocks) {
+        const int64_t row = item * LPB + g;
+        const bool active = row < A.n_lines;
+        const int64_t base = row * N;
+        const int64_t next = item + A.grid_blocks;
+        const bool has_next = next < n_items;
+
+        // 1. inverse x-DFT of every line, parked at this thread's own positions
+        for (int l = 0; l < L; ++l) {
+            cp_async_wait_pending(L - 1 - l);
+            __syncthreads();
+            C* Sl = Sb + (l * LPB + g) * PS;
+            C v[E];
 #pragma unroll
-        for (int c = 0; c < D; ++c) sE[c][0] = sE[c][1] = sJ[c][0] = sJ[c][1] = 0;
+            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+            if (mode != MODE_ROW_FIRST) LineFFT<T, N, E, Cfg::RMAX, true>::run(v, Xb, t, A.tw);
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int64_t idx = base + t + TL * m;
-            const bool inc = A.mask[idx] != 0;
-            C q[D], Ev[D], Jv[D];
+            for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
+        }
+
+        // 2. pointwise scheme update and volume averages on real-space values
+        if (active) {
+            T sE[D][2], sJ[D][2], sE2 = 0;
 #pragma unroll
-            for (int c = 0; c < D; ++c) q[c] = v[c][m];
-            pw.apply(q, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, A.Ntot, Ev, Jv,
-                     mode != MODE_ROW_OUTPUT);
+            for (int c = 0; c < D; ++c) sE[c][0] = sE[c][1] = sJ[c][0] = sJ[c][1] = 0;
+            const bool wst = mode != MODE_ROW_OUTPUT;
+#pragma unroll 4
+            for (int m = 0; m < E; ++m) {
+                const int pos = t + TL * m;
+                const int64_t idx = base + pos;
+                const bool inc = Mb[g * N + pos] != 0;
+                if (A.packed) {
+                    C* zp = Sb + g * PS + pos;
+                    C z = *zp, Ez, Jz;
+                    pointwise_packed<T>(A.k, z, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, Ez, Jz,
+                                        wst);
+                    *zp = z;
+                    sE[0][0] += Ez.x;
+                    sE[1][0] += Ez.y;
+                    sJ[0][0] += Jz.x;
+                    sJ[1][0] += Jz.y;
+                    sE2 += Ez.x * Ez.x + Ez.y * Ez.y;
+                    if (mode == MODE_ROW_OUTPUT) {
+                        A.Eout[idx] = mkc(Ez.x, (T)0);
+                        A.Eout[A.Ntot + idx] = mkc(Ez.y, (T)0);
+                    }
+                } else {
+                    C q[D], Ev[D], Jv[D];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) q[c] = Sb[(c * LPB + g) * PS + pos];
+                    pointwise<T, D>(A.k, q, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, A.Ntot, Ev,
+                                    Jv, wst);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        Sb[(c * LPB + g) * PS + pos] = q[c];
+                        sE[c][0] += Ev[c].x;
+                        sE[c][1] += Ev[c].y;
+                        sJ[c][0] += Jv[c].x;
+                        sJ[c][1] += Jv[c].y;
+                        sE2 += Ev[c].x * Ev[c].x + Ev[c].y * Ev[c].y;
+                        if (mode == MODE_ROW_OUTPUT) A.Eout[c * A.Ntot + idx] = Ev[c];
+                    }
+                }
+            }
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                v[c][m] = q[c];
-                sE[c][0] += Ev[c].x;
-                sE[c][1] += Ev[c].y;
-                sJ[c][0] += Jv[c].x;
-                sJ[c][1] += Jv[c].y;
-                sE2 += Ev[c].x * Ev[c].x + Ev[c].y * Ev[c].y;
-                if (mode == MODE_ROW_OUTPUT) A.Eout[c * A.Ntot + idx] = Ev[c];
+                acc[4 * c + 0] += (double)sE[c][0];
+                acc[4 * c + 1] += (double)sE[c][1];
+                acc[4 * c + 2] += (double)sJ[c][0];
+                acc[4 * c + 3] += (double)sJ[c][1];
             }
+            acc[4 * D] += (double)sE2;
         }
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            acc[4 * c + 0] = (double)sE[c][0];
-            acc[4 * c + 1] = (double)sE[c][1];
-            acc[4 * c + 2] = (double)sJ[c][0];
-            acc[4 * c + 3] = (double)sJ[c][1];
-        }
-        acc[4 * D] = (double)sE2;
-    }
 
-    if (mode != MODE_ROW_OUTPUT) {
+        // 3. forward x-DFT and store; the next item's line l is staged as soon as
+        //    every thread has read line l of this item
+        if (mode != MODE_ROW_OUTPUT) {
+            for (int l = 0; l < L; ++l) {
+                C* Sl = Sb + (l * LPB + g) * PS;
+                C v[E];
 #pragma unroll
-        for (int c = 0; c < D; ++c) LineFFT<T, N, E, Cfg::RMAX, false>::run(v[c], sm, t, A.tw);
-        if (active) {
+                for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+                __syncthreads();
+                if (has_next) prefetch_line(next, l);
+                LineFFT<T, N, E, Cfg::RMAX, false>::run(v, Xb, t, A.tw);
+                if (active) {
 #pragma unroll
-            for (int c = 0; c < D; ++c)
-#pragma unroll
-                for (int m = 0; m < E; ++m) A.X[c * A.Ntot + base + t + TL * m] = v[c][m];
+                    for (int m = 0; m < E; ++m) A.X[l * A.Ntot + base + t + TL * m] = v[m];
+                }
+            }
+        } else {
+            __syncthreads();
+            if (has_next)
+                for (int l = 0; l < L; ++l) prefetch_line(next, l);
         }
     }
+    cp_async_wait_all();
     block_reduce_store<NV>(acc, A.partials + (int64_t)blockIdx.x * NV);
 }
 
 // ---------------------------------------------------------------------------
-// Gamma multiply on one frequency: out = A v + B Gamma(k) v (k != 0),
-// out = A0 v + ce e (k = 0); coefficients carry the 1/N of the inverse DFT.
+// Gamma multiply on one frequency: out = a v + b Gamma(k) v (k != 0),
+// out = a0 v + ce e (k = 0); a, b, a0 carry the 1/N of the inverse DFT.
+// TRIG: Gamma(k) = k k^T/|k|^2 (Eq. J11), 0 if a component is at the Nyquist
+// index; FD: Gamma(k) = u u^H/|u|^2 with u_a = exp(2 pi i k_a/n_a) - 1.
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-__device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], const PassArgs<T>& A,
-                                            const SchemeParams& P) {
+__device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], const PassArgs<T>& A) {
     using C = cx<T>;
+    const KConst<T>& K = A.k;
     bool zero = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) zero = zero && (ki[a] == 0);
-    const T s = (T)P.inv_ntot;
     if (zero) {
-        const C a0 = mkc((T)(P.g_a0[0] * P.inv_ntot), (T)(P.g_a0[1] * P.inv_ntot));
-        const C ce = mkc((T)P.g_ce[0], (T)P.g_ce[1]);
 #pragma unroll
-        for (int c = 0; c < D; ++c) v[c] = cadd(cmul(a0, v[c]), cscale(ce, (T)P.e[c]));
+        for (int c = 0; c < D; ++c) v[c] = cadd(cmul(K.g_a0, v[c]), cscale(K.g_ce, K.e[c]));
         return;
     }
-    const C ga = mkc((T)P.g_a[0] * s, (T)P.g_a[1] * s);
-    const C gb = mkc((T)P.g_b[0] * s, (T)P.g_b[1] * s);
     C u[D];
     bool nyq = false;
-    if (P.green == GREEN_TRIG) {
+    if (K.green == GREEN_TRIG) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
             const int n = A.n[a];
@@ -342,91 +514,214 @@ __device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], c
 #pragma unroll
         for (int a = 0; a < D; ++a) u[a] = A.fd[a][ki[a]];
     }
-    C out[D];
     if (nyq) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) out[c] = cmul(ga, v[c]);
-    } else {
-        T nrm = 0;
-        C dot = mkc((T)0, (T)0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            nrm += u[a].x * u[a].x + u[a].y * u[a].y;
-            dot = cadd(dot, cmulc(v[a], u[a]));    // conj(u_a) v_a
-        }
-        const C proj = cscale(cmul(gb, dot), (T)1 / nrm);
-#pragma unroll
-        for (int c = 0; c < D; ++c) out[c] = cadd(cmul(ga, v[c]), cmul(proj, u[c]));
+        for (int c = 0; c < D; ++c) v[c] = cmul(K.g_a, v[c]);
+        return;
     }
+    T nrm = 0;
+    C dot = mkc((T)0, (T)0);
 #pragma unroll
-    for (int c = 0; c < D; ++c) v[c] = out[c];
+    for (int a = 0; a < D; ++a) {
+        nrm += u[a].x * u[a].x + u[a].y * u[a].y;
+        dot = cadd(dot, cmulc(v[a], u[a]));    // conj(u_a) v_a
+    }
+    const C proj = cscale(cmul(K.g_b, dot), (T)1 / nrm);
+#pragma unroll
+    for (int c = 0; c < D; ++c) v[c] = cadd(cmul(K.g_a, v[c]), cmul(proj, u[c]));
+}
+
+// Packed 2-D Gamma step on a Hermitian pair: z1 = Z(k), z2 = Z(-k) with
+// Z = F_x + i F_y the transform of two real fields.  F_x(k) = (z1 + conj z2)/2,
+// F_y(k) = (z1 - conj z2)/(2i); after the (real-coefficient) Gamma step the
+// outputs are repacked as Z'(k) = F'_x(k) + i F'_y(k) and
+// Z'(-k) = conj F'_x(k) + i conj F'_y(k).
+template <typename T>
+__device__ __forceinline__ void gamma_packed(cx<T>& z1, cx<T>& z2, int kx, int ky, const PassArgs<T>& A) {
+    using C = cx<T>;
+    const KConst<T>& K = A.k;
+    const C tx = mkc((z1.x + z2.x) * (T)0.5, (z1.y - z2.y) * (T)0.5);
+    const C ty = mkc((z1.y + z2.y) * (T)0.5, (z2.x - z1.x) * (T)0.5);
+    C ox, oy;
+    if (kx == 0 && ky == 0) {
+        ox = mkc(K.g_a0.x * tx.x + K.g_ce.x * K.e[0], K.g_a0.x * tx.y);
+        oy = mkc(K.g_a0.x * ty.x + K.g_ce.x * K.e[1], K.g_a0.x * ty.y);
+    } else {
+        C ux, uy;
+        bool nyq = false;
+        if (K.green == GREEN_TRIG) {
+            const int nx = A.n[0], ny = A.n[1];
+            nyq = (kx == nx / 2) || (ky == ny / 2);
+            ux = mkc((T)(kx < nx / 2 ? kx : kx - nx), (T)0);
+            uy = mkc((T)(ky < ny / 2 ? ky : ky - ny), (T)0);
+        } else {
+            ux = A.fd[0][kx];
+            uy = A.fd[1][ky];
+        }
+        ox = cscale(tx, K.g_a.x);
+        oy = cscale(ty, K.g_a.x);
+        if (!nyq) {
+            const T nrm = ux.x * ux.x + ux.y * ux.y + uy.x * uy.x + uy.y * uy.y;
+            const C dot = cadd(cmulc(tx, ux), cmulc(ty, uy));
+            const C proj = cscale(dot, K.g_b.x / nrm);
+            ox = cadd(ox, cmul(proj, ux));
+            oy = cadd(oy, cmul(proj, uy));
+        }
+    }
+    z1 = mkc(ox.x - oy.y, ox.y + oy.x);
+    z2 = mkc(ox.x + oy.y, oy.x - ox.y);
 }
 
 // ---------------------------------------------------------------------------
-// Strided pass: lines along y (or z) with element stride ls; each block takes
-// COLS adjacent line starts and every component (one thread group per line).
+// Strided pass: lines along y (or z) with element stride ls.  Work item =
+// COLS line starts (one per thread group): in the complex layout COLS adjacent
+// line starts of one outer slab with their d component lines; in the packed
+// 2-D layout COLS Hermitian column pairs (kx, nx - kx), the partner column
+// staged with reversed row order so that position k of its transform holds
+// Z(-kx, -k).  Columns 0 and nx/2 are their own partners.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int D>
-__global__ void __launch_bounds__(ColCfg<T, N, D>::THREADS)
+__global__ void __launch_bounds__(ColCfg<T, N, D>::THREADS, ColCfg<T, N, D>::MINB)
 col_pass(const PassArgs<T> A) {
     using Cfg = ColCfg<T, N, D>;
     using C = cx<T>;
-    constexpr int E = Cfg::E, TL = Cfg::TL, COLS = Cfg::COLS, G = Cfg::G;
+    constexpr int E = Cfg::E, TL = Cfg::TL, COLS = Cfg::COLS;
+    constexpr int PS = Cfg::P::S, PX = Cfg::P::X;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (A.ctrl->skipB) return;
     const int mode = A.mode;
+    const bool packed = A.packed != 0;
 
-    const int g = threadIdx.x % G, t = threadIdx.x / G;
-    const int col = g % COLS, comp = g / COLS;
-    C* sm = reinterpret_cast<C*>(smem_raw) + g * LinePad<N>::size;
+    C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][COLS][PS]
+    const int g = threadIdx.x / TL, t = threadIdx.x % TL;
+    C* Xb = reinterpret_cast<C*>(smem_raw + Cfg::S_BYTES) + g * PX;
+    const int L = packed ? 2 : D;
+    const int nx = A.n[0];
+    const int64_t cblocks = packed ? (nx / 2 + COLS) / COLS : A.n_inner / COLS;
+    const int64_t n_items = cblocks * (packed ? 1 : A.n_outer);
 
-    const int64_t cblocks = A.n_inner / COLS;
-    const int64_t outer = blockIdx.x / cblocks;
-    const int64_t inner0 = (blockIdx.x % cblocks) * COLS;
-    const int64_t base = comp * A.Ntot + outer * A.outer_stride + inner0 + col;
+    // complex layout: first line start of an item
+    auto item_base = [&](int64_t item) { return (item / cblocks) * A.outer_stride + (item % cblocks) * COLS; };
+    // packed layout: column of slot `l` of pair j (slot 1 is the partner)
+    auto pair_col = [&](int64_t j, int l) { return l == 0 ? (int)j : (int)((nx - j) % nx); };
 
-    C v[E];
+    auto prefetch_line = [&](int64_t item, int l) {
+        const int64_t b0 = packed ? 0 : item_base(item);
+        for (int i = threadIdx.x; i < COLS * N; i += Cfg::THREADS) {
+            const int col = i % COLS, r = i / COLS;
+            C* dst = Sb + (l * COLS + col) * PS + r;
+            const C* src;
+            if (packed) {
+                const int64_t j = item * COLS + col;
+                if (j > nx / 2) continue;
+                const int row = l == 0 ? r : (N - r) % N;
+                src = A.X + pair_col(j, l) + (int64_t)row * A.ls;
+            } else {
+                src = A.X + l * A.Ntot + b0 + col + (int64_t)r * A.ls;
+            }
+            if constexpr (sizeof(C) == 16) cp_async16(dst, src);
+            else cp_async8(dst, src);
+        }
+        cp_async_commit();
+    };
+    auto store_line = [&](int64_t item, int l, const C (&v)[E]) {
+        if (packed) {
+            const int64_t j = item * COLS + g;
+            if (j > nx / 2) return;
+            const bool self = (j == 0) || (j == nx / 2);
+            if (l == 1 && self) return;
+            C* dst = A.X + pair_col(j, l);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = A.X[base + (int64_t)(t + TL * m) * A.ls];
-
-    if (mode == MODE_COL_INV) {
-        LineFFT<T, N, E, Cfg::RMAX, true>::run(v, sm, t, A.tw);
-    } else {
-        LineFFT<T, N, E, Cfg::RMAX, false>::run(v, sm, t, A.tw);
-        if (mode == MODE_COL_GAMMA) {
-            const SchemeParams& P = *A.prm;
-            __syncthreads();
+            for (int m = 0; m < E; ++m) {
+                const int r = t + TL * m;
+                const int row = l == 0 ? r : (N - r) % N;
+                dst[(int64_t)row * A.ls] = v[m];
+            }
+        } else {
+            C* dst = A.X + l * A.Ntot + item_base(item) + g;
 #pragma unroll
-            for (int m = 0; m < E; ++m) sm[pad16(t + TL * m)] = v[m];
+            for (int m = 0; m < E; ++m) dst[(int64_t)(t + TL * m) * A.ls] = v[m];
+        }
+    };
+
+    int64_t item = blockIdx.x;
+    if (item < n_items)
+        for (int l = 0; l < L; ++l) prefetch_line(item, l);
+    for (; item < n_items; item += A.grid_blocks) {
+        const int64_t next = item + A.grid_blocks;
+        const bool has_next = next < n_items;
+        if (mode != MODE_COL_GAMMA) {
+            // forward-only or inverse-only transforms (3-D y passes)
+            for (int l = 0; l < L; ++l) {
+                cp_async_wait_pending(L - 1 - l);
+                __syncthreads();
+                C v[E];
+                C* Sl = Sb + (l * COLS + g) * PS;
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+                __syncthreads();
+                if (has_next) prefetch_line(next, l);
+                if (mode == MODE_COL_INV) LineFFT<T, N, E, Cfg::RMAX, true>::run(v, Xb, t, A.tw);
+                else LineFFT<T, N, E, Cfg::RMAX, false>::run(v, Xb, t, A.tw);
+                store_line(item, l, v);
+            }
+            continue;
+        }
+        // 1. forward transforms, parked at own positions
+        for (int l = 0; l < L; ++l) {
+            cp_async_wait_pending(L - 1 - l);
             __syncthreads();
-            C* lines = reinterpret_cast<C*>(smem_raw);
-            for (int idx = threadIdx.x; idx < COLS * N; idx += blockDim.x) {
-                const int cc = idx % COLS, kl = idx / COLS;
-                int ki[3] = {0, 0, 0};
-                const int64_t inner = inner0 + cc;
-                if (A.line_axis == 1) {            // 2-D: inner = kx, line = ky
-                    ki[0] = (int)inner;
-                    ki[1] = kl;
-                } else {                            // 3-D z pass: inner = kx + nx ky, line = kz
-                    ki[0] = (int)(inner % A.n[0]);
-                    ki[1] = (int)(inner / A.n[0]);
-                    ki[2] = kl;
-                }
+            C v[E];
+            C* Sl = Sb + (l * COLS + g) * PS;
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+            LineFFT<T, N, E, Cfg::RMAX, false>::run(v, Xb, t, A.tw);
+#pragma unroll
+            for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
+        }
+        // 2. Gamma multiply at own positions
+        if (packed) {
+            const int kx = (int)(item * COLS + g);
+            C* S0 = Sb + g * PS;
+            C* S1 = Sb + (COLS + g) * PS;
+#pragma unroll 4
+            for (int m = 0; m < E; ++m) {
+                const int kl = t + TL * m;
+                C z1 = S0[kl], z2 = S1[kl];
+                gamma_packed<T>(z1, z2, kx <= nx / 2 ? kx : 0, kl, A);
+                S0[kl] = z1;
+                S1[kl] = z2;
+            }
+        } else {
+            const int64_t inner = (item % cblocks) * COLS + g;
+            const bool two_d = A.line_axis == 1;   // 2-D: inner = kx, line = ky; 3-D z: inner = kx + nx ky
+            const int kx = two_d ? (int)inner : (int)(inner % nx);
+            const int ky0 = two_d ? 0 : (int)(inner / nx);
+#pragma unroll 4
+            for (int m = 0; m < E; ++m) {
+                const int kl = t + TL * m;
+                const int ki[3] = {kx, two_d ? kl : ky0, two_d ? 0 : kl};
                 C q[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) q[c] = lines[(cc + COLS * c) * LinePad<N>::size + pad16(kl)];
-                gamma_apply<T, D>(q, ki, A, P);
+                for (int c = 0; c < D; ++c) q[c] = Sb[(c * COLS + g) * PS + kl];
+                gamma_apply<T, D>(q, ki, A);
 #pragma unroll
-                for (int c = 0; c < D; ++c) lines[(cc + COLS * c) * LinePad<N>::size + pad16(kl)] = q[c];
+                for (int c = 0; c < D; ++c) Sb[(c * COLS + g) * PS + kl] = q[c];
             }
-            __syncthreads();
+        }
+        // 3. inverse transforms and stores; stage the next item line by line
+        for (int l = 0; l < L; ++l) {
+            C v[E];
+            C* Sl = Sb + (l * COLS + g) * PS;
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m)];
-            LineFFT<T, N, E, Cfg::RMAX, true>::run(v, sm, t, A.tw);
+            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+            __syncthreads();
+            if (has_next) prefetch_line(next, l);
+            LineFFT<T, N, E, Cfg::RMAX, true>::run(v, Xb, t, A.tw);
+            store_line(item, l, v);
         }
     }
-#pragma unroll
-    for (int m = 0; m < E; ++m) A.X[base + (int64_t)(t + TL * m) * A.ls] = v[m];
+    cp_async_wait_all();
 }
 
 }  // namespace lsfft

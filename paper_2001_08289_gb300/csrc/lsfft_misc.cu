@@ -6,13 +6,22 @@
 
 namespace lsfft {
 
+// Initial state.  Complex layout: Q = iq e, S = is e, T = it e (S, T on phase 1).
+// Packed real layout (d = 2): one plane z = iq (e_x + i e_y), with S = i s and
+// T = i tau stored as s = Im(is) (e_x + i e_y), tau = Im(it) (e_x + i e_y).
 template <typename T>
 __global__ void init_state_kernel(cx<T>* __restrict__ X, cx<T>* __restrict__ S, cx<T>* __restrict__ Tf,
-                                  const uint8_t* __restrict__ mask, const SchemeParams* __restrict__ prm,
-                                  int64_t Ntot, int d) {
-    const SchemeParams& P = *prm;
+                                  const uint8_t* __restrict__ mask, const SchemeParams P, int64_t Ntot, int d,
+                                  int packed) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Ntot; i += (int64_t)gridDim.x * blockDim.x) {
         const bool inc = mask[i] != 0;
+        if (packed) {
+            const double q = inc ? P.iq_in[0] : P.iq_out[0];
+            X[i] = mkc((T)(q * P.e[0]), (T)(q * P.e[1]));
+            if (S) S[i] = inc ? mkc((T)(P.is_in[1] * P.e[0]), (T)(P.is_in[1] * P.e[1])) : mkc((T)0, (T)0);
+            if (Tf) Tf[i] = inc ? mkc((T)(P.it_in[1] * P.e[0]), (T)(P.it_in[1] * P.e[1])) : mkc((T)0, (T)0);
+            continue;
+        }
         const double* q = inc ? P.iq_in : P.iq_out;
         for (int c = 0; c < d; ++c) {
             const double e = P.e[c];
@@ -28,7 +37,7 @@ __global__ void init_state_kernel(cx<T>* __restrict__ X, cx<T>* __restrict__ S, 
 constexpr int FIN_THREADS = 256;
 
 __global__ void __launch_bounds__(FIN_THREADS)
-finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const SchemeParams* __restrict__ prm,
+finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const SchemeParams P,
                 Ctrl* __restrict__ ctrl, double* __restrict__ hist, int final_mode) {
     __shared__ double tot[16];
     __shared__ double red[FIN_THREADS / 32];
@@ -51,7 +60,6 @@ finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const 
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
-    const SchemeParams& P = *prm;
     const int d = P.d;
     // sigma_k = (<J>.e) / (<E>.e); the 1/N factors cancel
     double je_re = 0, je_im = 0, ee_re = 0, ee_im = 0;
@@ -105,24 +113,24 @@ finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const 
 }
 
 template <typename T>
-cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams* prm, int64_t Ntot,
-                        int d, int sm_count, cudaStream_t s) {
+cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams& prm, int64_t Ntot,
+                        int d, int packed, int sm_count, cudaStream_t s) {
     int64_t blocks = (Ntot + 255) / 256;
     const int64_t cap = (int64_t)sm_count * 8;
     if (blocks > cap) blocks = cap;
-    init_state_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, S, Tf, mask, prm, Ntot, d);
+    init_state_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, S, Tf, mask, prm, Ntot, d, packed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams* prm, Ctrl* ctrl,
+cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
                             double* hist, int final_mode, cudaStream_t s) {
     finalize_kernel<<<1, FIN_THREADS, 0, s>>>(partials, nblocks, nv, prm, ctrl, hist, final_mode);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_init<float>(cx<float>*, cx<float>*, cx<float>*, const uint8_t*, const SchemeParams*,
-                                        int64_t, int, int, cudaStream_t);
-template cudaError_t launch_init<double>(cx<double>*, cx<double>*, cx<double>*, const uint8_t*, const SchemeParams*,
-                                         int64_t, int, int, cudaStream_t);
+template cudaError_t launch_init<float>(cx<float>*, cx<float>*, cx<float>*, const uint8_t*, const SchemeParams&,
+                                        int64_t, int, int, int, cudaStream_t);
+template cudaError_t launch_init<double>(cx<double>*, cx<double>*, cx<double>*, const uint8_t*, const SchemeParams&,
+                                         int64_t, int, int, int, cudaStream_t);
 
 }  // namespace lsfft

@@ -16,16 +16,17 @@ struct Geom {
     int threads = 0;     // threads per block
     int per_block = 0;   // rows (row pass) or line starts (strided pass) per block
     int smem = 0;        // dynamic shared memory bytes
+    int blocks_per_sm = 0;   // resident blocks per SM (after OP_PREPARE)
     bool supported = false;
 };
 
 enum { OP_QUERY = 0, OP_PREPARE = 1, OP_LAUNCH = 2 };
 
 template <typename T>
-cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams* prm, int64_t Ntot,
-                        int d, int sm_count, cudaStream_t s);
+cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams& prm, int64_t Ntot,
+                        int d, int packed, int sm_count, cudaStream_t s);
 
-cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams* prm, Ctrl* ctrl,
+cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
                             double* hist, int final_mode, cudaStream_t s);
 
 }  // namespace lsfft

@@ -82,17 +82,19 @@ def test_parity_2d_long_lines(L, shape):
     pass (the kernels with the largest shared-memory and register footprints)."""
     mask = random_mask(shape, 0.25, seed=sum(shape))
     e = np.array([1.0, 0.0])
-    precs = ["fp32"] + (["fp64"] if max(shape) <= 4096 or shape[1] == 8192 else [])
+    precs = ["fp32"] + (["fp64"] if max(shape) <= 4096 else [])
     for prec in precs:
         for scheme in ("ms", "em_sub"):
             _compare(L, mask, 10.0, e, scheme, "fd", prec, 6, ab=(0.05, 20.0))
 
 
-def test_fp64_rejects_8192_columns(L):
-    with L.Grid(np.zeros((8192, 16), np.uint8)) as g:
-        with pytest.raises(L.LsfftError) as ei:
-            g.solve(2.0, [1.0, 0.0], precision="fp64")
-        assert ei.value.status == L.EINVAL
+def test_fp64_rejects_8192_point_lines(L):
+    """FP64 supports line lengths up to 4096 on every axis (shared-memory bound)."""
+    for shape in ((8192, 16), (16, 8192)):
+        with L.Grid(np.zeros(shape, np.uint8)) as g:
+            with pytest.raises(L.LsfftError) as ei:
+                g.solve(2.0, [1.0, 0.0], precision="fp64")
+            assert ei.value.status == L.EINVAL
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -186,3 +188,23 @@ def test_divergence_and_invalid_arguments(L):
             assert ei.value.status == L.EINVAL
         with pytest.raises(L.LsfftError):
             g.solve(1.0, [0.0, 0.0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_packed_real_layout_used_and_agrees_with_complex_layout(L, prec):
+    """Real sigma_1 in 2-D runs the packed layout (E_x + i E_y in one plane); a
+    negligible imaginary part forces the complex layout: the two must agree."""
+    mask = random_mask((64, 128), 0.3, seed=3)
+    e = [0.8, 0.6]
+    with L.Grid(mask) as g:
+        for scheme in ("ms", "em", "ms_sub", "em_sub"):
+            kw = dict(scheme=scheme, precision=prec, green="fd", tol=0.0, max_iter=12, alpha=0.05, beta=20.0)
+            rp = g.solve(10.0, e, **kw)
+            rc = g.solve(complex(10.0, 1e-300), e, **kw)
+            assert rp.packed and not rc.packed
+            tol = 1e-12 if prec == "fp64" else 1e-6
+            assert np.max(np.abs(rp.hist_sigma - rc.hist_sigma) / np.abs(rc.hist_sigma)) < tol
+            Ep, Ec = rp.field_numpy(), rc.field_numpy()
+            assert np.linalg.norm(Ep - Ec) / np.linalg.norm(Ec) < (1e-12 if prec == "fp64" else 1e-5)
+    with L.Grid(square_array_mask(16, d=3)) as g:
+        assert not g.solve(5.0, [1.0, 0.0, 0.0], max_iter=3, tol=0.0).packed
