@@ -19,7 +19,7 @@
  *   - Every function returns an lsfft_status (0 = success) unless stated.
  *   - Grids are d = 2 or 3 dimensional with n[a] points along axis a, where
  *     n[0] is the fastest-varying (x) axis.  Each n[a] is a power of two in
- *     [16, 8192] (3-D: [16, 512]); in LSFFT_FP64 each n[a] <= 4096.
+ *     [16, 8192] (3-D: [16, 512]); in LSFFT_FP64, n[0] <= 4096.
  *     N = n[0] n[1] (n[2]).
  *   - Phase masks are uint8[N], x fastest (index x + n0*(y + n1*z)); a non-zero
  *     byte marks phase 1 (conductivity sigma_1), zero marks the matrix (1).

@@ -464,7 +464,12 @@ cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
     else col_dispatch<T, 3>(g->logn[axis], OP_QUERY, nullptr, nullptr, &geo);
     const int64_t items = A->packed ? (g->n[0] / 2 + geo.per_block) / geo.per_block   // Hermitian column pairs
                                     : (A->n_inner / geo.per_block) * A->n_outer;
-    A->grid_blocks = (int)persistent_blocks(g, items, geo.blocks_per_sm);
+    if (geo.cluster > 0) {
+        const int64_t ncl = items < geo.max_clusters ? items : (geo.max_clusters > 0 ? geo.max_clusters : 1);
+        A->grid_blocks = (int)(ncl * geo.cluster);
+    } else {
+        A->grid_blocks = (int)persistent_blocks(g, items, geo.blocks_per_sm);
+    }
     if (g->d == 2) return col_dispatch<T, 2>(g->logn[axis], OP_LAUNCH, A, g->stream, nullptr);
     return col_dispatch<T, 3>(g->logn[axis], OP_LAUNCH, A, g->stream, nullptr);
 }
@@ -759,7 +764,7 @@ int check_and_setup(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsf
     }
     const bool fp32 = o->precision == LSFFT_FP32;
     if (!(fp32 ? col_supported<float>(g) : col_supported<double>(g))) {
-        g_last_error = "grid size not supported in this precision (FP64: line lengths up to 4096)";
+        g_last_error = "grid size not supported in this precision (FP64: x lines up to 4096 points)";
         return LSFFT_EINVAL;
     }
     std::string why = build_params(g, s1, e, o, g->prm_host);

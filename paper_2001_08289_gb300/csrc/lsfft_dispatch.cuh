@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lsfft_cluster.cuh"
 #include "lsfft_kernels.cuh"
 #include "lsfft_misc.h"
 
@@ -39,28 +40,58 @@ cudaError_t row_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
 
 template <typename T, int N, int D>
 cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
-    using Cfg = ColCfg<T, N, D>;
-    static int bps = 0;
-    if constexpr (!Cfg::SUPPORTED) {
-        if (op == OP_QUERY) g->supported = false;
-        return op == OP_QUERY ? cudaSuccess : cudaErrorInvalidValue;
-    } else {
+    if constexpr (D == 2 && CluCfg<T, N>::SUPPORTED) {
+        // long 2-D columns: cluster kernel (item = W adjacent columns or column pairs)
+        using Cfg = CluCfg<T, N>;
+        static int max_clusters = 0;
         if (op == OP_QUERY) {
             g->threads = Cfg::THREADS;
-            g->per_block = Cfg::COLS;
+            g->per_block = Cfg::W;
             g->smem = Cfg::SMEM;
-            g->blocks_per_sm = bps;
+            g->blocks_per_sm = 1;
+            g->cluster = Cfg::CL;
+            g->max_clusters = max_clusters;
             g->supported = true;
             return cudaSuccess;
         }
         if (op == OP_PREPARE) {
-            cudaError_t e = cudaFuncSetAttribute(col_pass<T, N, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(col_pass_cluster<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  Cfg::SMEM);
             if (e != cudaSuccess) return e;
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass<T, N, D>, Cfg::THREADS, Cfg::SMEM);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(Cfg::CL, 1, 1);
+            cfg.blockDim = dim3(Cfg::THREADS, 1, 1);
+            cfg.dynamicSmemBytes = Cfg::SMEM;
+            return cudaOccupancyMaxActiveClusters(&max_clusters, (const void*)col_pass_cluster<T, N>, &cfg);
         }
-        col_pass<T, N, D><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
+        col_pass_cluster<T, N><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
         return cudaGetLastError();
+    } else {
+        using Cfg = ColCfg<T, N, D>;
+        static int bps = 0;
+        if constexpr (!Cfg::SUPPORTED) {
+            if (op == OP_QUERY) g->supported = false;
+            return op == OP_QUERY ? cudaSuccess : cudaErrorInvalidValue;
+        } else {
+            if (op == OP_QUERY) {
+                g->threads = Cfg::THREADS;
+                g->per_block = Cfg::COLS;
+                g->smem = Cfg::SMEM;
+                g->blocks_per_sm = bps;
+                g->cluster = 0;
+                g->supported = true;
+                return cudaSuccess;
+            }
+            if (op == OP_PREPARE) {
+                cudaError_t e = cudaFuncSetAttribute(col_pass<T, N, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     Cfg::SMEM);
+                if (e != cudaSuccess) return e;
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass<T, N, D>, Cfg::THREADS,
+                                                                     Cfg::SMEM);
+            }
+            col_pass<T, N, D><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
+            return cudaGetLastError();
+        }
     }
 }
 

@@ -17,8 +17,8 @@
 // collide in banks.
 //
 // Twiddles: FP32 uses sincospif() for W^{(j mod NS)} once per butterfly and
-// forms the other powers by balanced complex products; FP64 reads them from a
-// table W_N^k built on the host in double precision.
+// forms the other powers as products of W^{jm}, W^{2jm}, W^{4jm}, W^{8jm};
+// FP64 reads them from a table W_L^k built on the host in double precision.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -120,7 +120,8 @@ struct LineFFT {
     static_assert(N % E == 0, "E must divide N");
 
     template <int R>
-    __device__ __forceinline__ static void twiddle(C (&a)[R], int jm, int span, const C* __restrict__ tw) {
+    __device__ __forceinline__ static void twiddle(C (&a)[R], int jm, int span, const C* __restrict__ tw,
+                                                   int tws) {
         // a[r] *= W_span^{jm r}, forward W = exp(-2 pi i / span)
         if constexpr (sizeof(T) == 4) {
             // W^(jm r) from the bases W^(jm), W^(2 jm), W^(4 jm), W^(8 jm): each power is a
@@ -146,7 +147,7 @@ struct LineFFT {
                 a[r] = cmul(a[r], w);
             }
         } else {
-            const int step = (N / span) * jm;
+            const int step = (N / span) * jm * tws;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
                 C w = tw[step * r];
@@ -157,7 +158,8 @@ struct LineFFT {
     }
 
     template <int NS>
-    __device__ __forceinline__ static void stage(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw) {
+    __device__ __forceinline__ static void stage(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
+                                                 int tws) {
         constexpr int REM = N / NS;
         constexpr int R = REM >= RMAX ? RMAX : REM;
         constexpr bool LAST = (NS * R == N);
@@ -170,7 +172,7 @@ struct LineFFT {
             C a[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) a[r] = v[i + r * B];
-            if constexpr (NS > 1) twiddle<R>(a, j % NS, NS * R, tw);
+            if constexpr (NS > 1) twiddle<R>(a, j % NS, NS * R, tw, tws);
             dft<R, INV>(a);
             if constexpr (LAST) {
 #pragma unroll
@@ -185,14 +187,17 @@ struct LineFFT {
             __syncthreads();
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m)];
-            stage<NS * R>(v, sm, t, tw);
+            stage<NS * R>(v, sm, t, tw, tws);
         }
     }
 
     // Must be called by every thread of the block (it contains __syncthreads()
-    // whenever N > RMAX); threads of inactive lines pass dummy data.
-    __device__ __forceinline__ static void run(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw) {
-        stage<1>(v, sm, t, tw);
+    // whenever N > RMAX); threads of inactive lines pass dummy data.  FP64:
+    // `tw` holds W_L^k of a length L = N * tws (tws = 1 unless the line is a
+    // decimated part of a longer one).
+    __device__ __forceinline__ static void run(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
+                                               int tws = 1) {
+        stage<1>(v, sm, t, tw, tws);
     }
 };
 

@@ -17,6 +17,8 @@ struct Geom {
     int per_block = 0;   // rows (row pass) or line starts (strided pass) per block
     int smem = 0;        // dynamic shared memory bytes
     int blocks_per_sm = 0;   // resident blocks per SM (after OP_PREPARE)
+    int cluster = 0;         // > 0: cluster kernel with this many blocks per cluster
+    int max_clusters = 0;    // co-resident clusters (after OP_PREPARE)
     bool supported = false;
 };
 

@@ -82,19 +82,31 @@ def test_parity_2d_long_lines(L, shape):
     pass (the kernels with the largest shared-memory and register footprints)."""
     mask = random_mask(shape, 0.25, seed=sum(shape))
     e = np.array([1.0, 0.0])
-    precs = ["fp32"] + (["fp64"] if max(shape) <= 4096 else [])
+    precs = ["fp32"] + (["fp64"] if shape[1] <= 4096 else [])
     for prec in precs:
         for scheme in ("ms", "em_sub"):
             _compare(L, mask, 10.0, e, scheme, "fd", prec, 6, ab=(0.05, 20.0))
 
 
-def test_fp64_rejects_8192_point_lines(L):
-    """FP64 supports line lengths up to 4096 on every axis (shared-memory bound)."""
-    for shape in ((8192, 16), (16, 8192)):
-        with L.Grid(np.zeros(shape, np.uint8)) as g:
-            with pytest.raises(L.LsfftError) as ei:
-                g.solve(2.0, [1.0, 0.0], precision="fp64")
-            assert ei.value.status == L.EINVAL
+@pytest.mark.parametrize("shape", [(8192, 16), (4096, 32), (2048, 64)])
+def test_parity_long_columns_complex_sigma(L, shape):
+    """Long columns with complex sigma_1 (complex layout on the cluster strided pass)."""
+    mask = random_mask(shape, 0.3, seed=shape[0])
+    e = np.array([0.6, 0.8])
+    precs = ["fp32", "fp64"]
+    for prec in precs:
+        for scheme in ("ms", "em_sub"):
+            _compare(L, mask, 2.0 + 1.5j, e, scheme, "fd", prec, 6, ab=(0.05, 20.0))
+            _compare(L, mask, 2.0 + 1.5j, e, scheme, "trig", prec, 4, ab=(0.05, 20.0))
+
+
+def test_fp64_rejects_8192_point_rows(L):
+    """FP64 supports rows (x lines) up to 4096 points (shared-memory bound of the
+    row pass); 8192-point columns run on the cluster strided pass."""
+    with L.Grid(np.zeros((16, 8192), np.uint8)) as g:
+        with pytest.raises(L.LsfftError) as ei:
+            g.solve(2.0, [1.0, 0.0], precision="fp64")
+        assert ei.value.status == L.EINVAL
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
