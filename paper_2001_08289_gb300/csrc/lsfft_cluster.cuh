@@ -69,6 +69,10 @@ col_pass_cluster(const PassArgs<T> A) {
     const int nx = A.n[0];
     const int64_t n_items = packed ? (nx / 2 + W) / W : nx / W;
 
+    C* Yr[CL];                                          // the item buffers of every block of the cluster
+#pragma unroll
+    for (int p = 0; p < CL; ++p) Yr[p] = cluster.map_shared_rank(Y, p);
+
     // column, component plane and row order of line (s, w) of an item
     struct LineRef {
         int col;
@@ -100,26 +104,32 @@ col_pass_cluster(const PassArgs<T> A) {
         const int lr = q + CL * j;
         return r.reversed ? (N - lr) % N : lr;
     };
-    // stage slot s (W lines) of an item: lanes run over the W adjacent columns first
+    // stage / store slot s (W lines) of an item: lanes run over the W adjacent
+    // columns first.  THREADS is a multiple of W, so a thread keeps one column
+    // w = threadIdx.x % W for the whole loop and only the row advances.
+    static_assert(Cfg::THREADS % W == 0, "thread count must be a multiple of W");
+    const int wt = threadIdx.x % W;
+    const int j0 = threadIdx.x / W;
+    constexpr int JSTEP = Cfg::THREADS / W;
     auto prefetch_slot = [&](int64_t item, int s) {
-        for (int i = threadIdx.x; i < W * M; i += Cfg::THREADS) {
-            const int w = i % W, j = i / W;
-            const LineRef r = line_ref(item, s, w);
-            if (!r.load) continue;
-            C* dst = Y + (s * W + w) * YP + j;
-            const C* src = A.X + r.plane * A.Ntot + r.col + (int64_t)phys_row(r, j) * A.ls;
-            if constexpr (sizeof(C) == 16) cp_async16(dst, src);
-            else cp_async8(dst, src);
+        const LineRef r = line_ref(item, s, wt);
+        if (r.load) {
+            C* dst = Y + (s * W + wt) * YP;
+            const C* src = A.X + r.plane * A.Ntot + r.col;
+            for (int j = j0; j < M; j += JSTEP) {
+                const C* sp = src + (int64_t)phys_row(r, j) * A.ls;
+                if constexpr (sizeof(C) == 16) cp_async16(dst + j, sp);
+                else cp_async8(dst + j, sp);
+            }
         }
         cp_async_commit();
     };
     auto store_slot = [&](int64_t item, int s) {
-        for (int i = threadIdx.x; i < W * M; i += Cfg::THREADS) {
-            const int w = i % W, j = i / W;
-            const LineRef r = line_ref(item, s, w);
-            if (!r.store) continue;
-            A.X[r.plane * A.Ntot + r.col + (int64_t)phys_row(r, j) * A.ls] = Y[(s * W + w) * YP + j];
-        }
+        const LineRef r = line_ref(item, s, wt);
+        if (!r.store) return;
+        const C* src = Y + (s * W + wt) * YP;
+        C* dst = A.X + r.plane * A.Ntot + r.col;
+        for (int j = j0; j < M; j += JSTEP) dst[(int64_t)phys_row(r, j) * A.ls] = src[j];
     };
     // W_N^(p k) for p = 0..CL-1 (forward sign)
     auto twiddles = [&](int k, C (&w)[CL]) {
@@ -166,10 +176,7 @@ col_pass_cluster(const PassArgs<T> A) {
             for (int s = 0; s < LS; ++s) {
                 C y[CL];
 #pragma unroll
-                for (int p = 0; p < CL; ++p) {
-                    const C* Yp = cluster.map_shared_rank(Y, p);
-                    y[p] = cmul(Yp[(s * W + w) * YP + k], tw[p]);
-                }
+                for (int p = 0; p < CL; ++p) y[p] = cmul(Yr[p][(s * W + w) * YP + k], tw[p]);
                 // 4-point DFT over p: x[m] = sum_p y[p] (-i)^(p m)
                 const C a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
                 const C b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
@@ -208,10 +215,7 @@ col_pass_cluster(const PassArgs<T> A) {
                 y[1] = cadd(a1, b1r);
                 y[3] = csub(a1, b1r);
 #pragma unroll
-                for (int p = 0; p < CL; ++p) {
-                    C* Yp = cluster.map_shared_rank(Y, p);
-                    Yp[(s * W + w) * YP + k] = cmulc(y[p], tw[p]);
-                }
+                for (int p = 0; p < CL; ++p) Yr[p][(s * W + w) * YP + k] = cmulc(y[p], tw[p]);
             }
         }
         cluster.sync();

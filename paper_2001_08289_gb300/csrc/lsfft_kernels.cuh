@@ -375,9 +375,18 @@ row_pass(const PassArgs<T> A) {
         cp_async_commit();
     };
 
-    double acc[NV];
+    // Running per-thread sums over items, compensated (Kahan) in the field
+    // precision: the FP64 pipe of the GPU is far slower than FP32, so in FP32
+    // mode doubles enter only in the block and grid reductions at the end.
+    T acc[NV], cmp[NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int i = 0; i < NV; ++i) acc[i] = cmp[i] = (T)0;
+    auto kahan_add = [&](int i, T x) {
+        const T y = x - cmp[i];
+        const T tsum = acc[i] + y;
+        cmp[i] = (tsum - acc[i]) - y;
+        acc[i] = tsum;
+    };
 
     int64_t item = blockIdx.x;
     if (item < n_items)
@@ -448,12 +457,12 @@ row_pass(const PassArgs<T> A) {
             }
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                acc[4 * c + 0] += (double)sE[c][0];
-                acc[4 * c + 1] += (double)sE[c][1];
-                acc[4 * c + 2] += (double)sJ[c][0];
-                acc[4 * c + 3] += (double)sJ[c][1];
+                kahan_add(4 * c + 0, sE[c][0]);
+                kahan_add(4 * c + 1, sE[c][1]);
+                kahan_add(4 * c + 2, sJ[c][0]);
+                kahan_add(4 * c + 3, sJ[c][1]);
             }
-            acc[4 * D] += (double)sE2;
+            kahan_add(4 * D, sE2);
         }
 
         // 3. forward x-DFT and store; the next item's line l is staged as soon as
@@ -479,7 +488,10 @@ row_pass(const PassArgs<T> A) {
         }
     }
     cp_async_wait_all();
-    block_reduce_store<NV>(acc, A.partials + (int64_t)blockIdx.x * NV);
+    double dacc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) dacc[i] = (double)acc[i] - (double)cmp[i];
+    block_reduce_store<NV>(dacc, A.partials + (int64_t)blockIdx.x * NV);
 }
 
 // ---------------------------------------------------------------------------
