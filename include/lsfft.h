@@ -163,6 +163,37 @@ int lsfft_prepare(lsfft_grid *grid, lsfft_c128 sigma1, const double *e, const ls
  * count < 0, or a grid without a prepared state (or whose last solve stopped). */
 int lsfft_launch_passes(lsfft_grid *grid, int kind, int count);
 
+/* Volume averages of a field without any device allocation.  The paper has
+ * no counterpart: this is a utility for callers that cannot call cudaMalloc,
+ * e.g. code that must not block (cudaMalloc/cudaFree may synchronise the
+ * device), code whose device memory is owned by another allocator under a
+ * fixed budget, or code running where allocation is not allowed.
+ * Inputs (device pointers, not copied): E_device, a complex field [d][N] in
+ * `precision` (the layout of lsfft_result.E_device); mask_device, uint8[N]
+ * (non-zero = phase 1, conductivity sigma1; zero = conductivity 1); e, d host
+ * doubles.  Output: out_device, 4*d + 3 doubles on the device:
+ *   out[4c+0], out[4c+1]  Re, Im <E_c>      out[4c+2], out[4c+3]  Re, Im <J_c>
+ *   out[4d] <|E|^2>      out[4d+1], out[4d+2]  Re, Im sigma_* = <J>.e / <E>.e
+ * with J = sigma E: what lsfft_solve reports for its field under LSFFT_MS, whose
+ * flux is sigma E at every iterate (the other schemes report their own flux
+ * estimate, which equals sigma E at convergence).
+ * The work is enqueued on cuda_stream (NULL = legacy default stream) and the
+ * call returns without waiting.  Block partial sums live in one file-scope
+ * __device__ array of 4096 x 16 doubles (512 KiB, held by every device that
+ * loads the library until the process exits), so N must not exceed
+ * 4096 * 65536 = 268,435,456 voxels (EINVAL otherwise).  Every call on a device
+ * shares that array and leaves its partial sums in it; calls whose kernels
+ * overlap on the GPU race, so serialise them (one stream, or events).  The
+ * first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (the only set-up; it allocates nothing): make that
+ * first call before any stream capture.  Errors: EINVAL (null pointer, d not
+ * in {2, 3}, unknown precision, n[a] < 1, N over the limit), ECUDA (lookup or
+ * launch failure); lsfft_noalloc_last_error() gives the message. */
+int lsfft_field_averages_noalloc(int d, const int64_t n[3], const void *E_device, int precision,
+                                 const uint8_t *mask_device, lsfft_c128 sigma1, const double *e,
+                                 double *out_device, void *cuda_stream);
+const char *lsfft_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

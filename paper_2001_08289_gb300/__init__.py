@@ -26,7 +26,7 @@ __all__ = [
     "LsfftError", "Opts", "Result", "Grid", "load_library", "library_path",
     "lsfft_version", "lsfft_last_error", "lsfft_strerror", "lsfft_create_grid", "lsfft_create_grid_device",
     "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
-    "lsfft_prepare", "lsfft_launch_passes", "make_opts",
+    "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "make_opts",
     "SCHEMES", "GREENS",
 ]
 
@@ -100,6 +100,9 @@ def load_library():
     lib.lsfft_free_result.restype = None
     lib.lsfft_prepare.argtypes = [C.c_void_p, _C128, C.POINTER(C.c_double), C.POINTER(Opts)]
     lib.lsfft_launch_passes.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    lib.lsfft_field_averages_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64), C.c_void_p, C.c_int, C.c_void_p,
+                                                 _C128, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]
+    lib.lsfft_noalloc_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -178,6 +181,19 @@ def lsfft_prepare(grid: int, sigma1: complex, e, opts: Opts) -> None:
     s1 = complex(sigma1)
     ev = (C.c_double * 3)(*[float(x) for x in list(e) + [0.0] * (3 - len(e))])
     _check(load_library().lsfft_prepare(C.c_void_p(grid), _C128(s1.real, s1.imag), ev, C.byref(opts)))
+
+
+def lsfft_field_averages_noalloc(d: int, n, E_ptr: int, precision: int, mask_ptr: int, sigma1: complex, e,
+                                 out_ptr: int, stream: int = 0) -> None:
+    """Volume averages of a device field into out_ptr (4 d + 3 device doubles)
+    with no device allocation; asynchronous on `stream`."""
+    s1 = complex(sigma1)
+    ev = (C.c_double * 3)(*[float(x) for x in list(e) + [0.0] * (3 - len(e))])
+    lib = load_library()
+    st = lib.lsfft_field_averages_noalloc(int(d), _dims(n), C.c_void_p(E_ptr), int(precision), C.c_void_p(mask_ptr),
+                                          _C128(s1.real, s1.imag), ev, C.c_void_p(out_ptr), C.c_void_p(stream or None))
+    if st != OK:
+        raise LsfftError(st, f"{lsfft_strerror(st)}: {lib.lsfft_noalloc_last_error().decode()}")
 
 
 def lsfft_launch_passes(grid: int, kind: int, count: int) -> None:
