@@ -83,6 +83,7 @@ typedef struct {
 
 typedef struct {
     lsfft_c128 sigma_star;     /* sigma_* of the returned field: <J>.e / <E>.e              */
+    lsfft_c128 sigma1;         /* the inclusion conductivity of the solve                   */
     lsfft_c128 mean_E[3];      /* <E> of the returned field (d entries used)               */
     lsfft_c128 mean_J[3];      /* <J> of the returned field                                */
     int iters;                 /* number of updates applied                                 */
@@ -147,6 +148,28 @@ int lsfft_copy_field(const lsfft_result *res, void *dst, int dst_on_device);
 /* Free the result's host history and device field. */
 void lsfft_free_result(lsfft_result *res);
 
+/* Per-voxel conductivity sigma(x) (complex, N entries, host or device
+ * pointer; copied).  Subsequent solves on the grid use sigma(x) instead of the
+ * two-phase 1 + (sigma_1 - 1) chi(x) of the mask, with the MS or EM scheme only
+ * (the substituted schemes of Eq. J36-J44 need two phases: EINVAL) and
+ * reference medium sigma0 (0 = automatic: (min + max)/2 of Re sigma for MS,
+ * sqrt(min max) for EM).  The mask is kept for lsfft_gradient's d/d sigma_1.
+ * sigma = NULL returns to the two-phase medium.  EINVAL for non-finite
+ * entries. */
+int lsfft_set_sigma_field(lsfft_grid *grid, const lsfft_c128 *sigma, int on_device, lsfft_c128 sigma0);
+
+/* Gradient of sigma_* for the field of `res` (a result of this grid): the first
+ * variation of the energy <sigma E.E> = sigma_* |e|^2 of Eq. J12/J13 (E.E
+ * bilinear, no conjugation, so complex conductivities are covered) gives
+ *   d sigma_* / d sigma(x) = E(x).E(x) / (N |e|^2),
+ *   d sigma_* / d sigma_1  = sum_x chi(x) E(x).E(x) / (N |e|^2).
+ * grad_device (complex [N] in the result's precision) receives the first, or
+ * may be NULL; dsigma1 and energy (may be NULL) receive the second and the
+ * variational estimate <sigma E.E> / |e|^2 of sigma_*.  Both formulas hold at
+ * the converged field.  Synchronises the grid's stream. */
+int lsfft_gradient(lsfft_grid *grid, const lsfft_result *res, const double *e, void *grad_device,
+                   lsfft_c128 *dsigma1, lsfft_c128 *energy);
+
 /* Diagnostics and benchmarking: set up the state of a solve (constants of
  * Eq. J1/J2/J3/J24, the initial field and one full update, exactly as
  * lsfft_solve starts) and return without further iterations.  Same arguments
@@ -162,6 +185,27 @@ int lsfft_prepare(lsfft_grid *grid, lsfft_c128 sigma1, const double *e, const ls
  * state in place; no stop test runs.  Returns EINVAL for an unknown kind,
  * count < 0, or a grid without a prepared state (or whose last solve stopped). */
 int lsfft_launch_passes(lsfft_grid *grid, int kind, int count);
+
+/* Estimate of the pole interval [-beta, -alpha] (section "Estimating the
+ * parameters alpha and beta").  The singularities of sigma_*(sigma_1) are the
+ * poles 1 - 1/m_n with m_n the eigenvalues of chi Gamma_1 chi weighted by
+ * |u_n^H chi e|^2; `steps` Lanczos steps from chi e on the GPU (matrix-vector
+ * products through the same FFT passes as the solver, FP64 recurrence
+ * scalars) give the Gauss nodes theta_i and weights w_i of that spectral
+ * measure, and alpha = 1/theta_max - 1, beta = 1/theta_min - 1 over nodes with
+ * w_i > cutoff * sum(w) and theta_i > 1e-14.  nodes, weights (host, >= steps
+ * doubles each) and n_nodes may be NULL.  Uses the grid's stream and
+ * synchronises it; allocates three field-sized vectors for the duration.
+ * EINVAL for bad arguments (steps outside [2, 4096], cutoff outside [0, 1), e
+ * zero), ENOTCONV if no node passes the cutoff. */
+int lsfft_lanczos_hull(lsfft_grid *grid, const double *e, int green, int precision, int steps, double cutoff,
+                       double *alpha, double *beta, double *nodes, double *weights, int *n_nodes);
+
+/* Host helper: Gauss quadrature of a Jacobi matrix (diagonal a[m],
+ * off-diagonal b[m-1]): its eigenvalues nodes[m] and the squared first
+ * components of its normalised eigenvectors first2[m] (implicit QL iteration).
+ * EINVAL for bad arguments, ENOTCONV if the iteration stalls. */
+int lsfft_tridiag_gauss(int m, const double *a, const double *b, double *nodes, double *first2);
 
 /* Volume averages of a field without any device allocation.  The paper has
  * no counterpart: this is a utility for callers that cannot call cudaMalloc,

@@ -26,7 +26,8 @@ __all__ = [
     "LsfftError", "Opts", "Result", "Grid", "load_library", "library_path",
     "lsfft_version", "lsfft_last_error", "lsfft_strerror", "lsfft_create_grid", "lsfft_create_grid_device",
     "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
-    "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "make_opts",
+    "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
+    "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "make_opts",
     "SCHEMES", "GREENS",
 ]
 
@@ -63,7 +64,8 @@ class Opts(C.Structure):
 
 class _Result(C.Structure):
     """Mirror of lsfft_result."""
-    _fields_ = [("sigma_star", _C128), ("mean_E", _C128 * 3), ("mean_J", _C128 * 3), ("iters", C.c_int),
+    _fields_ = [("sigma_star", _C128), ("sigma1", _C128), ("mean_E", _C128 * 3), ("mean_J", _C128 * 3),
+                ("iters", C.c_int),
                 ("status", C.c_int), ("hist_len", C.c_int), ("hist_sigma_re", C.POINTER(C.c_double)),
                 ("hist_sigma_im", C.POINTER(C.c_double)), ("hist_rel_change", C.POINTER(C.c_double)),
                 ("hist_field_norm", C.POINTER(C.c_double)), ("solve_ms", C.c_double),
@@ -103,6 +105,14 @@ def load_library():
     lib.lsfft_field_averages_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64), C.c_void_p, C.c_int, C.c_void_p,
                                                  _C128, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]
     lib.lsfft_noalloc_last_error.restype = C.c_char_p
+    lib.lsfft_lanczos_hull.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_int, C.c_int, C.c_double,
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    lib.lsfft_tridiag_gauss.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.lsfft_set_sigma_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int, _C128]
+    lib.lsfft_gradient.argtypes = [C.c_void_p, C.POINTER(_Result), C.POINTER(C.c_double), C.c_void_p,
+                                   C.POINTER(_C128), C.POINTER(_C128)]
     _lib = lib
     return lib
 
@@ -194,6 +204,51 @@ def lsfft_field_averages_noalloc(d: int, n, E_ptr: int, precision: int, mask_ptr
                                           _C128(s1.real, s1.imag), ev, C.c_void_p(out_ptr), C.c_void_p(stream or None))
     if st != OK:
         raise LsfftError(st, f"{lsfft_strerror(st)}: {lib.lsfft_noalloc_last_error().decode()}")
+
+
+def lsfft_tridiag_gauss(a, b):
+    """Gauss nodes and squared first eigenvector components of the Jacobi
+    matrix with diagonal a and off-diagonal b (host computation)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    m = a.size
+    b = np.ascontiguousarray(b if m > 1 else np.zeros(1), dtype=np.float64)
+    nodes = np.empty(m)
+    first2 = np.empty(m)
+    p = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load_library().lsfft_tridiag_gauss(m, p(a), p(b), p(nodes), p(first2)))
+    return nodes, first2
+
+
+def lsfft_lanczos_hull(grid: int, e, green="trig", precision="fp32", steps: int = 60, cutoff: float = 1e-10):
+    """(alpha, beta, nodes, weights): pole interval estimate from `steps` Lanczos steps."""
+    ev = (C.c_double * 3)(*[float(x) for x in list(e) + [0.0] * (3 - len(e))])
+    g = GREENS[green] if isinstance(green, str) else int(green)
+    pr = {"fp32": FP32, "fp64": FP64}[precision] if isinstance(precision, str) else int(precision)
+    nodes = np.empty(steps)
+    weights = np.empty(steps)
+    al, be = C.c_double(), C.c_double()
+    m = C.c_int()
+    p = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load_library().lsfft_lanczos_hull(C.c_void_p(grid), ev, g, pr, int(steps), float(cutoff), C.byref(al),
+                                             C.byref(be), p(nodes), p(weights), C.byref(m)))
+    return al.value, be.value, nodes[:m.value].copy(), weights[:m.value].copy()
+
+
+def lsfft_set_sigma_field(grid: int, sigma_ptr, on_device: bool, sigma0: complex = 0.0) -> None:
+    """Per-voxel complex conductivity (N lsfft_c128 values at sigma_ptr), or None
+    to return to the two-phase medium."""
+    s0 = complex(sigma0)
+    _check(load_library().lsfft_set_sigma_field(C.c_void_p(grid), C.c_void_p(sigma_ptr) if sigma_ptr else None,
+                                                int(bool(on_device)), _C128(s0.real, s0.imag)))
+
+
+def lsfft_gradient(grid: int, res, e, grad_ptr=None):
+    """(d sigma_*/d sigma_1, <sigma E.E>/|e|^2); d sigma_*/d sigma(x) into grad_ptr if given."""
+    ev = (C.c_double * 3)(*[float(x) for x in list(e) + [0.0] * (3 - len(e))])
+    d1, en = _C128(), _C128()
+    _check(load_library().lsfft_gradient(C.c_void_p(grid), res, ev, C.c_void_p(grad_ptr) if grad_ptr else None,
+                                         C.byref(d1), C.byref(en)))
+    return complex(d1.re, d1.im), complex(en.re, en.im)
 
 
 def lsfft_launch_passes(grid: int, kind: int, count: int) -> None:
@@ -294,6 +349,30 @@ class Grid:
 
     def prepare(self, sigma1, e, **kw) -> None:
         lsfft_prepare(self.handle, sigma1, e, make_opts(**kw))
+
+    def set_sigma_field(self, sigma, sigma0: complex = 0.0) -> None:
+        """Per-voxel conductivity: array of shape `shape` (numpy, or a CUDA torch
+        tensor), any real or complex dtype; None returns to the two-phase medium."""
+        if sigma is None:
+            lsfft_set_sigma_field(self.handle, None, False)
+            return
+        if hasattr(sigma, "is_cuda") and sigma.is_cuda:
+            import torch
+
+            t = sigma.to(torch.complex128).contiguous()
+            torch.cuda.current_stream().synchronize()
+            lsfft_set_sigma_field(self.handle, t.data_ptr(), True, sigma0)
+        else:
+            a = np.ascontiguousarray(np.asarray(sigma), dtype=np.complex128)
+            lsfft_set_sigma_field(self.handle, a.ctypes.data, False, sigma0)
+
+    def gradient(self, result, e, grad_ptr=None):
+        """(d sigma_*/d sigma_1, energy estimate); d sigma_*/d sigma(x) into grad_ptr."""
+        return lsfft_gradient(self.handle, result._ptr, e, grad_ptr)
+
+    def lanczos_hull(self, e, **kw):
+        """(alpha, beta, nodes, weights) of the pole measure seen from chi e."""
+        return lsfft_lanczos_hull(self.handle, e, **kw)
 
     def launch_passes(self, kind: int, count: int) -> None:
         lsfft_launch_passes(self.handle, kind, count)

@@ -6,8 +6,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <complex>
 #include <map>
+#include <vector>
 #include <string>
 #include <tuple>
 
@@ -86,6 +89,13 @@ struct lsfft_grid {
     void* fd[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // FD symbol per axis, FP32/FP64
     bool prepared[2] = {false, false};
     int packed = 0;                 // packed real layout for the current solve
+    // per-voxel conductivity mode (lsfft_set_sigma_field)
+    double2* sigma64 = nullptr;     // device copy, FP64 complex [N]
+    void* sigma_t = nullptr;        // the same in the precision of the last solve
+    int sigma_t_prec = -1;
+    double sig_min = 0.0, sig_max = 0.0;   // extremes of Re sigma
+    bool sig_real = false;
+    double sigma0_user[2] = {0.0, 0.0};
     int bench_prec = -1;            // precision of the state set up by lsfft_prepare (-1: none)
     int bench_st = 0;
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -304,6 +314,30 @@ std::string build_params(const lsfft_grid* g, cplx s1, const double* e, const ls
     for (int c = 0; c < g->d; ++c) P->e[c] = e[c];
     put(P->sigma1, s1);
     const cplx one(1.0, 0.0);
+    if (g->sigma64) {
+        // per-voxel conductivity: MS or EM with a reference medium sigma_0 (the
+        // caller's, else (min + max)/2 for MS and sqrt(min max) for EM over Re sigma)
+        if (o->scheme != LSFFT_MS && o->scheme != LSFFT_EM)
+            return "a per-voxel conductivity field needs the MS or EM scheme";
+        cplx s0(g->sigma0_user[0], g->sigma0_user[1]);
+        if (s0 == 0.0)
+            s0 = o->scheme == LSFFT_MS ? cplx((g->sig_min + g->sig_max) / 2.0, 0.0)
+                                       : cplx(std::sqrt(std::max(g->sig_min * g->sig_max, 0.0)), 0.0);
+        if (s0 == 0.0) return "reference medium sigma_0 = 0";
+        put(P->s0, s0);
+        put(P->inv_s0, one / s0);
+        if (o->scheme == LSFFT_MS) {
+            put(P->g_b, cplx(-1.0));
+            put(P->g_ce, one);
+        } else {
+            put(P->inv2s0, one / (2.0 * s0));
+            put(P->g_a, one);
+            put(P->g_b, cplx(-2.0));
+            put(P->g_a0, one);
+            put(P->g_ce, 2.0 * s0);
+        }
+        return "";
+    }
     switch (o->scheme) {
         case LSFFT_MS: {   // Eq. J0-0 with sigma_0 = (sigma_1 + 1)/2 (Eq. J1)
             const cplx s0 = (s1 + one) / 2.0;
@@ -401,6 +435,8 @@ KConst<T> make_kconst(const SchemeParams& P) {
     K.w = kc<T>(P.w);
     K.inv2s0 = kc<T>(P.inv2s0);
     K.s1 = kc<T>(P.sigma1);
+    K.s0 = kc<T>(P.s0);
+    K.inv_s0 = kc<T>(P.inv_s0);
     K.g_a = kc<T>(P.g_a, P.inv_ntot);
     K.g_b = kc<T>(P.g_b, P.inv_ntot);
     K.g_a0 = kc<T>(P.g_a0, P.inv_ntot);
@@ -416,8 +452,9 @@ KConst<T> make_kconst(const SchemeParams& P) {
 // imaginary): then Q, J and E stay real and S, T purely imaginary.
 bool packed_layout(const lsfft_grid* g, const SchemeParams& P) {
     if (g->d != 2) return false;
+    if (g->sigma64 && !g->sig_real) return false;
     const double* re_only[] = {P.sigma1, P.a_in, P.a_out, P.k1, P.k2, P.tm1p1, P.p1, P.w, P.inv2s0,
-                               P.g_a, P.g_b, P.g_a0, P.g_ce, P.iq_in, P.iq_out};
+                               P.g_a, P.g_b, P.g_a0, P.g_ce, P.iq_in, P.iq_out, P.s0, P.inv_s0};
     for (const double* v : re_only)
         if (v[1] != 0.0) return false;
     const double* im_only[] = {P.p2, P.p3, P.k3, P.is_in, P.it_in};
@@ -435,6 +472,7 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
     A.S = st >= 1 ? (cx<T>*)g->S : nullptr;
     A.Tf = st >= 2 ? (cx<T>*)g->T : nullptr;
     A.mask = g->mask;
+    A.sigma = (g->sigma64 && g->sigma_t_prec == (int)(sizeof(T) == 8)) ? (const cx<T>*)g->sigma_t : nullptr;
     A.packed = g->packed;
     A.k = make_kconst<T>(*g->prm_host);
     A.ctrl = g->ctrl_dev;
@@ -568,16 +606,33 @@ int ensure_prepared(lsfft_grid* g) {
     return LSFFT_OK;
 }
 
+// The per-voxel conductivity in the precision of the solve (converted once).
+template <typename T>
+int prepare_sigma(lsfft_grid* g) {
+    if (!g->sigma64 || g->sigma_t_prec == (int)(sizeof(T) == 8)) return LSFFT_OK;
+    CK(cudaStreamSynchronize(g->stream));
+    cudaFree(g->sigma_t);
+    g->sigma_t = nullptr;
+    g->sigma_t_prec = -1;
+    CK(cudaMalloc(&g->sigma_t, (size_t)g->N * sizeof(cx<T>)));
+    CK(launch_convert_field<T>((cx<T>*)g->sigma_t, g->sigma64, g->N, g->sm_count, g->stream));
+    g->sigma_t_prec = (int)(sizeof(T) == 8);
+    return LSFFT_OK;
+}
+
 // Upload the constants, write the initial state and run the first update.
 template <typename T>
 int start_solve(lsfft_grid* g, int st) {
     int rc0 = ensure_prepared<T>(g);
     if (rc0 != LSFFT_OK) return rc0;
     const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
+    rc0 = prepare_sigma<T>(g);
+    if (rc0 != LSFFT_OK) return rc0;
     CK(cudaMemsetAsync(g->ctrl_dev, 0, sizeof(Ctrl), g->stream));
     CK(cudaEventRecord(g->ev0, g->stream));
     CK(launch_init<T>((cx<T>*)g->X, st >= 1 ? (cx<T>*)g->S : nullptr, st >= 2 ? (cx<T>*)g->T : nullptr, g->mask,
-                      *g->prm_host, g->N, g->d, g->packed, g->sm_count, g->stream));
+                      *g->prm_host, g->N, g->d, g->packed,
+                      g->sigma64 ? (const cx<T>*)g->sigma_t : nullptr, g->sm_count, g->stream));
     CK(launch_iteration<T>(g, st, nblocks, MODE_ROW_FIRST));
     return LSFFT_OK;
 }
@@ -585,6 +640,8 @@ int start_solve(lsfft_grid* g, int st) {
 template <typename T>
 int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     int rc = ensure_prepared<T>(g);   // shared-memory limits must be set before capture
+    if (rc != LSFFT_OK) return rc;
+    rc = prepare_sigma<T>(g);         // the captured kernels point at the converted field
     if (rc != LSFFT_OK) return rc;
     const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
     cudaGraphExec_t exec;
@@ -714,6 +771,8 @@ void lsfft_destroy_grid(lsfft_grid* g) {
     }
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
+    cudaFree(g->sigma64);
+    cudaFree(g->sigma_t);
     if (g->own_stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -795,6 +854,7 @@ int lsfft_solve(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_o
     lsfft_result* res = (lsfft_result*)calloc(1, sizeof(lsfft_result));
     if (!res) return LSFFT_ENOMEM;
     res->precision = o->precision;
+    res->sigma1 = sigma1;
     res->d = g->d;
     for (int a = 0; a < 3; ++a) res->n[a] = a < g->d ? g->n[a] : 1;
     rc = fp32 ? run_solve<float>(g, o, st, res) : run_solve<double>(g, o, st, res);
@@ -858,6 +918,340 @@ void lsfft_free_result(lsfft_result* res) {
     free(res->hist_rel_change);
     free(res->hist_field_norm);
     free(res);
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos estimate of the pole interval (section "Estimating the parameters
+// alpha and beta").  The poles of sigma_*(sigma_1) are 1 - 1/m_n, m_n the
+// eigenvalues of chi Gamma_1 chi weighted by |u_n^H chi e|^2; Lanczos from
+// chi e builds the Jacobi matrix of that spectral measure, whose eigenvalues
+// (Gauss nodes) and squared first eigenvector components give the weights.
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// Eigenvalues of the symmetric tridiagonal matrix (a diagonal, b off-diagonal)
+// and the first component of each normalised eigenvector, by the implicit QL
+// iteration with Wilkinson-type shifts.  Returns false if an eigenvalue needs
+// more than 60 sweeps.
+bool tridiag_eig(std::vector<double>& a, std::vector<double> b, std::vector<double>& first) {
+    const int m = (int)a.size();
+    b.resize(m, 0.0);
+    first.assign(m, 0.0);
+    first[0] = 1.0;   // row 0 of the accumulated rotation
+    for (int l = 0; l < m; ++l) {
+        int sweeps = 0;
+        for (;;) {
+            int k = l;
+            for (; k < m - 1; ++k) {
+                const double scale = std::fabs(a[k]) + std::fabs(a[k + 1]);
+                if (std::fabs(b[k]) <= 1e-15 * scale) break;
+            }
+            if (k == l) break;
+            if (++sweeps > 60) return false;
+            // shift from the trailing 2x2 block at l
+            double g = (a[l + 1] - a[l]) / (2.0 * b[l]);
+            double r = std::hypot(g, 1.0);
+            g = a[k] - a[l] + b[l] / (g + (g >= 0 ? r : -r));
+            double sn = 1.0, cs = 1.0, p = 0.0;
+            bool deflated = false;
+            for (int i = k - 1; i >= l; --i) {
+                const double f = sn * b[i], h = cs * b[i];
+                r = std::hypot(f, g);
+                b[i + 1] = r;
+                if (r == 0.0) {
+                    a[i + 1] -= p;
+                    b[k] = 0.0;
+                    deflated = true;
+                    break;
+                }
+                sn = f / r;
+                cs = g / r;
+                g = a[i + 1] - p;
+                r = (a[i] - g) * sn + 2.0 * cs * h;
+                p = sn * r;
+                a[i + 1] = g + p;
+                g = cs * r - h;
+                const double z = first[i + 1];
+                first[i + 1] = sn * first[i] + cs * z;
+                first[i] = cs * first[i] - sn * z;
+            }
+            if (deflated) continue;
+            a[l] -= p;
+            b[l] = g;
+            b[k] = 0.0;
+        }
+    }
+    return true;
+}
+
+template <typename T>
+int run_lanczos(lsfft_grid* g, const double* evec, int steps, std::vector<double>& al, std::vector<double>& be,
+                double* norm0_out) {
+    int rc = ensure_prepared<T>(g);
+    if (rc != LSFFT_OK) return rc;
+    const int64_t L = (int64_t)g->d * g->N;
+    const size_t bytes = (size_t)L * sizeof(cx<T>);
+    const int blocks = g->sm_count * 4;
+    cx<T>*V[3] = {nullptr, nullptr, nullptr};
+    double* part = nullptr;
+    double* scal = nullptr;
+    double* host = nullptr;
+    auto cleanup = [&]() {
+        for (auto& v : V) cudaFree(v);
+        cudaFree(part);
+        cudaFree(scal);
+        if (host) cudaFreeHost(host);
+    };
+    cudaError_t e0 = cudaSuccess;
+    for (auto& v : V)
+        if (e0 == cudaSuccess) e0 = cudaMalloc(&v, bytes);
+    if (e0 == cudaSuccess) e0 = cudaMalloc(&part, sizeof(double) * blocks);
+    if (e0 == cudaSuccess) e0 = cudaMalloc(&scal, sizeof(double) * 2);
+    if (e0 == cudaSuccess) e0 = cudaMallocHost(&host, sizeof(double) * 2);
+    if (e0 != cudaSuccess) {
+        cleanup();
+        return fail_cuda(e0, "lanczos buffers");
+    }
+    cx<T>* vprev = V[0];
+    cx<T>* v = V[1];
+    cx<T>* w = V[2];
+    auto read_scalar = [&](double* out) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(host, scal, sizeof(double), cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        *out = host[0];
+        return e;
+    };
+    cudaError_t e = cudaMemsetAsync(g->ctrl_dev, 0, sizeof(Ctrl), g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(vprev, 0, bytes, g->stream);
+    if (e == cudaSuccess) e = lanczos_init<T>(v, g->mask, g->N, g->d, evec, blocks, part, scal, g->stream);
+    double nrm2 = 0.0;
+    if (e == cudaSuccess) e = read_scalar(&nrm2);
+    if (e == cudaSuccess && nrm2 <= 0.0) {
+        cleanup();
+        g_last_error = "chi e vanishes (no inclusion voxel or e = 0)";
+        return LSFFT_EINVAL;
+    }
+    const double nrm0 = std::sqrt(nrm2);
+    *norm0_out = nrm0;
+    if (e == cudaSuccess) e = lanczos_scale<T>(v, v, 1.0 / nrm0, L, blocks, g->stream);
+    double beta_prev = 0.0;
+    for (int j = 0; j < steps && e == cudaSuccess; ++j) {
+        // w = chi Gamma_1 chi v: row pass (chi, forward x-DFT), strided pass(es)
+        // (forward, Gamma, inverse), row pass (inverse x-DFT, chi) into w
+        e = cudaMemcpyAsync(g->X, v, bytes, cudaMemcpyDeviceToDevice, g->stream);
+        if (e == cudaSuccess) e = launch_row<T>(g, 0, MODE_ROW_FIRST, nullptr);
+        if (e == cudaSuccess) e = launch_cols<T>(g, 0);
+        if (e == cudaSuccess) e = launch_row<T>(g, 0, MODE_ROW_OUTPUT, w);
+        double a_j = 0.0, b2 = 0.0;
+        if (e == cudaSuccess) e = lanczos_dot<T>(v, w, L, blocks, part, scal, g->stream);
+        if (e == cudaSuccess) e = read_scalar(&a_j);
+        if (e == cudaSuccess) e = lanczos_axpy_norm<T>(w, v, vprev, a_j, beta_prev, L, blocks, part, scal, g->stream);
+        if (e == cudaSuccess) e = read_scalar(&b2);
+        if (e != cudaSuccess) break;
+        al.push_back(a_j);
+        const double b_j = std::sqrt(std::max(b2, 0.0));
+        if (j == steps - 1 || b_j <= 1e-10) break;   // last step, or an invariant subspace was reached
+        be.push_back(b_j);
+        // rotate: vprev <- v, v <- w / b_j
+        cx<T>* old_prev = vprev;
+        vprev = v;
+        e = lanczos_scale<T>(old_prev, w, 1.0 / b_j, L, blocks, g->stream);
+        v = old_prev;
+        beta_prev = b_j;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail_cuda(e, "lanczos");
+    be.resize(al.size() > 0 ? al.size() - 1 : 0);
+    return LSFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lsfft_tridiag_gauss(int m, const double* a, const double* b, double* nodes, double* first2) {
+    if (m < 1 || !a || (m > 1 && !b) || !nodes || !first2) {
+        g_last_error = "lsfft_tridiag_gauss: bad arguments";
+        return LSFFT_EINVAL;
+    }
+    std::vector<double> d(a, a + m), off(m > 1 ? b : a, m > 1 ? b + (m - 1) : a), z;
+    if (!tridiag_eig(d, off, z)) {
+        g_last_error = "lsfft_tridiag_gauss: QL iteration did not converge";
+        return LSFFT_ENOTCONV;
+    }
+    for (int i = 0; i < m; ++i) {
+        nodes[i] = d[i];
+        first2[i] = z[i] * z[i];
+    }
+    return LSFFT_OK;
+}
+
+int lsfft_lanczos_hull(lsfft_grid* g, const double* e, int green, int precision, int steps, double cutoff,
+                       double* alpha, double* beta, double* nodes, double* weights, int* n_nodes) {
+    if (!g || !e || !alpha || !beta || (green != 0 && green != 1) || (precision != 0 && precision != 1) ||
+        steps < 2 || steps > 4096 || !(cutoff >= 0.0 && cutoff < 1.0)) {
+        g_last_error = "lsfft_lanczos_hull: bad arguments";
+        return LSFFT_EINVAL;
+    }
+    double e2 = 0.0;
+    for (int c = 0; c < g->d; ++c) e2 += e[c] * e[c];
+    if (!(e2 > 0.0) || !std::isfinite(e2)) {
+        g_last_error = "e must be finite and non-zero";
+        return LSFFT_EINVAL;
+    }
+    const bool fp32 = precision == LSFFT_FP32;
+    if (!(fp32 ? col_supported<float>(g) : col_supported<double>(g))) {
+        g_last_error = "grid size not supported in this precision";
+        return LSFFT_EINVAL;
+    }
+    // operator chi Gamma_1 chi: pointwise chi, Gamma step out = Gamma(k) v (k != 0), 0 at k = 0
+    SchemeParams* P = g->prm_host;
+    memset(P, 0, sizeof(*P));
+    P->scheme = SCHEME_MATVEC;
+    P->green = green;
+    P->d = g->d;
+    P->max_iter = 1;
+    P->consecutive = 1;
+    P->inv_ntot = 1.0 / (double)g->N;
+    for (int c = 0; c < g->d; ++c) P->e[c] = e[c];
+    P->g_b[0] = 1.0;
+    g->packed = 0;
+    g->bench_prec = -1;
+    int rc = ensure_workspace(g, precision, 0, 1);
+    if (rc != LSFFT_OK) return rc;
+    std::vector<double> al, be;
+    double nrm0 = 0.0;
+    rc = fp32 ? run_lanczos<float>(g, e, steps, al, be, &nrm0) : run_lanczos<double>(g, e, steps, al, be, &nrm0);
+    if (rc != LSFFT_OK) return rc;
+    const int m = (int)al.size();
+    std::vector<double> th(m), w2(m);
+    rc = lsfft_tridiag_gauss(m, al.data(), be.data(), th.data(), w2.data());
+    if (rc != LSFFT_OK) return rc;
+    double wsum = 0.0;
+    for (int i = 0; i < m; ++i) {
+        w2[i] *= nrm0 * nrm0;
+        wsum += w2[i];
+    }
+    double tmin = INFINITY, tmax = -INFINITY;
+    for (int i = 0; i < m; ++i) {
+        if (w2[i] > cutoff * wsum && th[i] > 1e-14) {
+            tmin = std::min(tmin, th[i]);
+            tmax = std::max(tmax, th[i]);
+        }
+    }
+    if (!(tmax > 0.0)) {
+        g_last_error = "no weighted Lanczos node above the cutoff";
+        return LSFFT_ENOTCONV;
+    }
+    *alpha = 1.0 / tmax - 1.0;
+    *beta = 1.0 / tmin - 1.0;
+    if (n_nodes) *n_nodes = m;
+    for (int i = 0; i < m; ++i) {
+        if (nodes) nodes[i] = th[i];
+        if (weights) weights[i] = w2[i];
+    }
+    return LSFFT_OK;
+}
+
+int lsfft_set_sigma_field(lsfft_grid* g, const lsfft_c128* sigma, int on_device, lsfft_c128 sigma0) {
+    if (!g) {
+        g_last_error = "null grid";
+        return LSFFT_EINVAL;
+    }
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    clear_graphs(g);
+    cudaFree(g->sigma64);
+    cudaFree(g->sigma_t);
+    g->sigma64 = nullptr;
+    g->sigma_t = nullptr;
+    g->sigma_t_prec = -1;
+    if (!sigma) return LSFFT_OK;   // back to the two-phase medium of the mask
+    const size_t bytes = (size_t)g->N * sizeof(lsfft_c128);
+    std::vector<lsfft_c128> h((size_t)g->N);
+    if (on_device) {
+        CK(cudaMemcpy(h.data(), sigma, bytes, cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(h.data(), sigma, bytes);
+    }
+    double mn = INFINITY, mx = -INFINITY;
+    bool real = true;
+    for (const auto& v : h) {
+        if (!std::isfinite(v.re) || !std::isfinite(v.im)) {
+            g_last_error = "sigma field must be finite";
+            return LSFFT_EINVAL;
+        }
+        mn = std::min(mn, v.re);
+        mx = std::max(mx, v.re);
+        real = real && v.im == 0.0;
+    }
+    CK(cudaMalloc(&g->sigma64, bytes));
+    CK(cudaMemcpy(g->sigma64, h.data(), bytes, cudaMemcpyHostToDevice));
+    g->sig_min = mn;
+    g->sig_max = mx;
+    g->sig_real = real && sigma0.im == 0.0;
+    g->sigma0_user[0] = sigma0.re;
+    g->sigma0_user[1] = sigma0.im;
+    return LSFFT_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int gradient_impl(lsfft_grid* g, const lsfft_result* res, const double* e, void* grad_device,
+                         lsfft_c128* dsigma1, lsfft_c128* energy) {
+    const int blocks = g->sm_count * 4;
+    double e2 = 0.0;
+    for (int c = 0; c < g->d; ++c) e2 += e[c] * e[c];
+    const cx<T>* sig = nullptr;
+    if (g->sigma64) {
+        if (g->sigma_t_prec != (int)(sizeof(T) == 8)) {
+            g_last_error = "the conductivity field was not prepared in the result's precision";
+            return LSFFT_EINVAL;
+        }
+        sig = (const cx<T>*)g->sigma_t;
+    }
+    CK(launch_gradient<T>((const cx<T>*)res->E_device, g->mask, sig, res->sigma1.re, res->sigma1.im, g->d, g->N,
+                          1.0 / ((double)g->N * e2), (cx<T>*)grad_device, blocks, g->partials, g->stream));
+    std::vector<double> h((size_t)blocks * 4);
+    CK(cudaMemcpyAsync(h.data(), g->partials, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = 0; b < blocks; ++b)
+        for (int v = 0; v < 4; ++v) acc[v] += h[(size_t)b * 4 + v];
+    if (dsigma1) {
+        dsigma1->re = acc[0] / ((double)g->N * e2);
+        dsigma1->im = acc[1] / ((double)g->N * e2);
+    }
+    if (energy) {
+        energy->re = acc[2] / ((double)g->N * e2);
+        energy->im = acc[3] / ((double)g->N * e2);
+    }
+    return LSFFT_OK;
+}
+
+extern "C" {
+
+int lsfft_gradient(lsfft_grid* g, const lsfft_result* res, const double* e, void* grad_device, lsfft_c128* dsigma1,
+                   lsfft_c128* energy) {
+    if (!g || !res || !e || !res->E_device || res->d != g->d) {
+        g_last_error = "lsfft_gradient: bad arguments";
+        return LSFFT_EINVAL;
+    }
+    for (int a = 0; a < g->d; ++a)
+        if (res->n[a] != g->n[a]) {
+            g_last_error = "lsfft_gradient: result and grid differ in size";
+            return LSFFT_EINVAL;
+        }
+    if (!g->partials) {
+        g_last_error = "lsfft_gradient: the grid has not solved yet";
+        return LSFFT_EINVAL;
+    }
+    return res->precision == LSFFT_FP32 ? gradient_impl<float>(g, res, e, grad_device, dsigma1, energy)
+                                        : gradient_impl<double>(g, res, e, grad_device, dsigma1, energy);
 }
 
 }  // extern "C"

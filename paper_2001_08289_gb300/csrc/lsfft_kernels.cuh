@@ -151,6 +151,7 @@ struct KConst {
     cx<T> k1, k2, k3, tm1p1;    // MS in H''
     cx<T> p1, p2, p3, w;        // EM in H''
     cx<T> inv2s0, s1;
+    cx<T> s0, inv_s0;           // per-voxel conductivity mode: reference medium and its inverse
     cx<T> g_a, g_b, g_a0;       // Gamma step coefficients, already divided by N
     cx<T> g_ce;                 // zero-mode source coefficient
     T e[3];
@@ -185,6 +186,13 @@ __device__ __forceinline__ void pointwise(const KConst<T>& K, cx<T> (&q)[D], boo
             E[c] = cmul(csub(q[c], wp), K.inv2s0);
             J[c] = cscale(cadd(q[c], wp), (T)0.5);
             q[c] = wp;
+        }
+    } else if (K.scheme == SCHEME_MATVEC) { // chi v (the operator chi Gamma_1 chi of the pole problem)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            E[c] = inc ? q[c] : mkc((T)0, (T)0);
+            J[c] = mkc((T)0, (T)0);
+            q[c] = E[c];
         }
     } else if (K.scheme == SCHEME_MS_SUB) { // Eq. J36, J42a: tau'' = (L''/sigma_0'' - 1) E''
         if (inc) {
@@ -308,6 +316,49 @@ __device__ __forceinline__ void pointwise_packed(const KConst<T>& K, cx<T>& z, b
     }
 }
 
+// Per-voxel conductivity sigma(x) (a medium with any number of phases), for the
+// Moulinec-Suquet and Eyre-Milton schemes with a caller-chosen reference sigma_0.
+template <typename T, int D>
+__device__ __forceinline__ void pointwise_field(const KConst<T>& K, cx<T> (&q)[D], cx<T> sg, cx<T> (&E)[D],
+                                                cx<T> (&J)[D]) {
+    using C = cx<T>;
+    if (K.scheme == SCHEME_MS) {            // tau = (sigma/sigma_0 - 1) E, J = sigma E
+        const C a = csub(cmul(sg, K.inv_s0), mkc((T)1, (T)0));
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            E[c] = q[c];
+            J[c] = cmul(sg, q[c]);
+            q[c] = cmul(a, q[c]);
+        }
+    } else {                                // W = (sigma - sigma_0)/(sigma + sigma_0)
+        const C num = csub(sg, K.s0), den = cadd(sg, K.s0);
+        const T dd = den.x * den.x + den.y * den.y;
+        const C W = cscale(cmulc(num, den), (T)1 / dd);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const C wp = cmul(W, q[c]);
+            E[c] = cmul(csub(q[c], wp), K.inv2s0);
+            J[c] = cscale(cadd(q[c], wp), (T)0.5);
+            q[c] = wp;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void pointwise_field_packed(const KConst<T>& K, cx<T>& z, T sg, cx<T>& E, cx<T>& J) {
+    if (K.scheme == SCHEME_MS) {
+        E = z;
+        J = cscale(z, sg);
+        z = cscale(z, sg * K.inv_s0.x - (T)1);
+    } else {
+        const T W = (sg - K.s0.x) / (sg + K.s0.x);
+        const cx<T> wp = cscale(z, W);
+        E = cscale(csub(z, wp), K.inv2s0.x);
+        J = cscale(cadd(z, wp), (T)0.5);
+        z = wp;
+    }
+}
+
 template <typename T>
 struct PassArgs {
     cx<T>* X;                 // state, [D][Ntot] (packed: plane 0 only)
@@ -315,6 +366,7 @@ struct PassArgs {
     cx<T>* Tf;                // H'' T component, [D][Ntot] (or null)
     cx<T>* Eout;              // output field, [D][Ntot] (row pass, output mode)
     const uint8_t* mask;      // [Ntot]
+    const cx<T>* sigma;       // per-voxel conductivity [Ntot] (MS / EM only), or null for two phases
     Ctrl* ctrl;
     double* partials;         // [gridDim.x][NV]
     const cx<T>* tw;          // FP64 twiddle table W_N^k of the pass's line length
@@ -425,8 +477,11 @@ row_pass(const PassArgs<T> A) {
                 if (A.packed) {
                     C* zp = Sb + g * PS + pos;
                     C z = *zp, Ez, Jz;
-                    pointwise_packed<T>(A.k, z, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, Ez, Jz,
-                                        wst);
+                    if (A.sigma)
+                        pointwise_field_packed<T>(A.k, z, A.sigma[idx].x, Ez, Jz);
+                    else
+                        pointwise_packed<T>(A.k, z, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, Ez,
+                                            Jz, wst);
                     *zp = z;
                     sE[0][0] += Ez.x;
                     sE[1][0] += Ez.y;
@@ -441,8 +496,11 @@ row_pass(const PassArgs<T> A) {
                     C q[D], Ev[D], Jv[D];
 #pragma unroll
                     for (int c = 0; c < D; ++c) q[c] = Sb[(c * LPB + g) * PS + pos];
-                    pointwise<T, D>(A.k, q, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, A.Ntot, Ev,
-                                    Jv, wst);
+                    if (A.sigma)
+                        pointwise_field<T, D>(A.k, q, A.sigma[idx], Ev, Jv);
+                    else
+                        pointwise<T, D>(A.k, q, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, A.Ntot,
+                                        Ev, Jv, wst);
 #pragma unroll
                     for (int c = 0; c < D; ++c) {
                         Sb[(c * LPB + g) * PS + pos] = q[c];

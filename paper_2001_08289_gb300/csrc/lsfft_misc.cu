@@ -12,9 +12,19 @@ namespace lsfft {
 template <typename T>
 __global__ void init_state_kernel(cx<T>* __restrict__ X, cx<T>* __restrict__ S, cx<T>* __restrict__ Tf,
                                   const uint8_t* __restrict__ mask, const SchemeParams P, int64_t Ntot, int d,
-                                  int packed) {
+                                  int packed, const cx<T>* __restrict__ sigma) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Ntot; i += (int64_t)gridDim.x * blockDim.x) {
         const bool inc = mask[i] != 0;
+        if (sigma) {   // per-voxel mode: MS starts from E = e, EM from P = (sigma + sigma_0) e
+            const double qr = P.scheme == SCHEME_EM ? (double)sigma[i].x + P.s0[0] : 1.0;
+            const double qi = P.scheme == SCHEME_EM ? (double)sigma[i].y + P.s0[1] : 0.0;
+            if (packed) {
+                X[i] = mkc((T)(qr * P.e[0]), (T)(qr * P.e[1]));
+            } else {
+                for (int c = 0; c < d; ++c) X[c * Ntot + i] = mkc((T)(qr * P.e[c]), (T)(qi * P.e[c]));
+            }
+            continue;
+        }
         if (packed) {
             const double q = inc ? P.iq_in[0] : P.iq_out[0];
             X[i] = mkc((T)(q * P.e[0]), (T)(q * P.e[1]));
@@ -114,11 +124,11 @@ finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const 
 
 template <typename T>
 cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams& prm, int64_t Ntot,
-                        int d, int packed, int sm_count, cudaStream_t s) {
+                        int d, int packed, const cx<T>* sigma, int sm_count, cudaStream_t s) {
     int64_t blocks = (Ntot + 255) / 256;
     const int64_t cap = (int64_t)sm_count * 8;
     if (blocks > cap) blocks = cap;
-    init_state_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, S, Tf, mask, prm, Ntot, d, packed);
+    init_state_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, S, Tf, mask, prm, Ntot, d, packed, sigma);
     return cudaGetLastError();
 }
 
@@ -129,8 +139,201 @@ cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const S
 }
 
 template cudaError_t launch_init<float>(cx<float>*, cx<float>*, cx<float>*, const uint8_t*, const SchemeParams&,
-                                        int64_t, int, int, int, cudaStream_t);
+                                        int64_t, int, int, const cx<float>*, int, cudaStream_t);
 template cudaError_t launch_init<double>(cx<double>*, cx<double>*, cx<double>*, const uint8_t*, const SchemeParams&,
-                                         int64_t, int, int, int, cudaStream_t);
+                                         int64_t, int, int, const cx<double>*, int, cudaStream_t);
+
+}  // namespace lsfft
+
+// ---------------------------------------------------------------------------
+// Lanczos vector kernels on flat complex arrays of length L (FP64 reductions).
+// ---------------------------------------------------------------------------
+namespace lsfft {
+
+constexpr int VEC_THREADS = 256;
+
+__device__ __forceinline__ void vec_block_sum(double x, double* __restrict__ out) {
+    __shared__ double red[VEC_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < VEC_THREADS / 32; ++w) s += red[w];
+        out[blockIdx.x] = s;
+    }
+}
+
+// v = chi e (d components), partial sums of |v|^2
+template <typename T>
+__global__ void vec_init_masked_e(cx<T>* __restrict__ v, const uint8_t* __restrict__ mask, int64_t N, int d, double e0,
+                                  double e1, double e2, double* __restrict__ partials) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)VEC_THREADS + threadIdx.x; i < N; i += (int64_t)gridDim.x * VEC_THREADS) {
+        const bool inc = mask[i] != 0;
+        const double e[3] = {e0, e1, e2};
+        for (int c = 0; c < d; ++c) {
+            const double val = inc ? e[c] : 0.0;
+            v[c * N + i] = mkc((T)val, (T)0);
+            acc += val * val;
+        }
+    }
+    vec_block_sum(acc, partials);
+}
+
+// partial sums of Re sum conj(a) b
+template <typename T>
+__global__ void vec_dot(const cx<T>* __restrict__ a, const cx<T>* __restrict__ b, int64_t L,
+                        double* __restrict__ partials) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)VEC_THREADS + threadIdx.x; i < L; i += (int64_t)gridDim.x * VEC_THREADS)
+        acc += (double)a[i].x * (double)b[i].x + (double)a[i].y * (double)b[i].y;
+    vec_block_sum(acc, partials);
+}
+
+// w <- w - alpha v - beta u, partial sums of |w|^2
+template <typename T>
+__global__ void vec_axpy_norm(cx<T>* __restrict__ w, const cx<T>* __restrict__ v, const cx<T>* __restrict__ u,
+                              double alpha, double beta, int64_t L, double* __restrict__ partials) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)VEC_THREADS + threadIdx.x; i < L; i += (int64_t)gridDim.x * VEC_THREADS) {
+        const double x = (double)w[i].x - alpha * (double)v[i].x - beta * (double)u[i].x;
+        const double y = (double)w[i].y - alpha * (double)v[i].y - beta * (double)u[i].y;
+        w[i] = mkc((T)x, (T)y);
+        acc += x * x + y * y;
+    }
+    vec_block_sum(acc, partials);
+}
+
+template <typename T>
+__global__ void vec_scale(cx<T>* __restrict__ dst, const cx<T>* __restrict__ src, double s, int64_t L) {
+    for (int64_t i = blockIdx.x * (int64_t)VEC_THREADS + threadIdx.x; i < L; i += (int64_t)gridDim.x * VEC_THREADS)
+        dst[i] = mkc((T)((double)src[i].x * s), (T)((double)src[i].y * s));
+}
+
+__global__ void vec_sum_partials(const double* __restrict__ partials, int n, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) s += partials[b];   // fixed order
+        out[0] = s;
+    }
+}
+
+template <typename T>
+cudaError_t lanczos_init(cx<T>* v, const uint8_t* mask, int64_t N, int d, const double* e, int blocks,
+                         double* partials, double* out, cudaStream_t s) {
+    vec_init_masked_e<T><<<blocks, VEC_THREADS, 0, s>>>(v, mask, N, d, e[0], e[1], d > 2 ? e[2] : 0.0, partials);
+    vec_sum_partials<<<1, 32, 0, s>>>(partials, blocks, out);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t lanczos_dot(const cx<T>* a, const cx<T>* b, int64_t L, int blocks, double* partials, double* out,
+                        cudaStream_t s) {
+    vec_dot<T><<<blocks, VEC_THREADS, 0, s>>>(a, b, L, partials);
+    vec_sum_partials<<<1, 32, 0, s>>>(partials, blocks, out);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t lanczos_axpy_norm(cx<T>* w, const cx<T>* v, const cx<T>* u, double alpha, double beta, int64_t L,
+                              int blocks, double* partials, double* out, cudaStream_t s) {
+    vec_axpy_norm<T><<<blocks, VEC_THREADS, 0, s>>>(w, v, u, alpha, beta, L, partials);
+    vec_sum_partials<<<1, 32, 0, s>>>(partials, blocks, out);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t lanczos_scale(cx<T>* dst, const cx<T>* src, double sc, int64_t L, int blocks, cudaStream_t s) {
+    vec_scale<T><<<blocks, VEC_THREADS, 0, s>>>(dst, src, sc, L);
+    return cudaGetLastError();
+}
+
+#define LSFFT_INST_VEC(T)                                                                                         \
+    template cudaError_t lanczos_init<T>(cx<T>*, const uint8_t*, int64_t, int, const double*, int, double*, double*, \
+                                         cudaStream_t);                                                           \
+    template cudaError_t lanczos_dot<T>(const cx<T>*, const cx<T>*, int64_t, int, double*, double*, cudaStream_t); \
+    template cudaError_t lanczos_axpy_norm<T>(cx<T>*, const cx<T>*, const cx<T>*, double, double, int64_t, int,    \
+                                              double*, double*, cudaStream_t);                                    \
+    template cudaError_t lanczos_scale<T>(cx<T>*, const cx<T>*, double, int64_t, int, cudaStream_t);
+LSFFT_INST_VEC(float)
+LSFFT_INST_VEC(double)
+
+}  // namespace lsfft
+
+// ---------------------------------------------------------------------------
+// Gradient of sigma_* (first variation of the energy <sigma E.E> = sigma_* |e|^2,
+// Eq. J12/J13): d sigma_*/d sigma(x) = E(x).E(x) / (N |e|^2) with the bilinear dot.
+// Also the sums sum_x chi(x) g(x) (= d sigma_*/d sigma_1) and <sigma E.E>/|e|^2.
+// ---------------------------------------------------------------------------
+namespace lsfft {
+
+template <typename T>
+__global__ void gradient_kernel(const cx<T>* __restrict__ E, const uint8_t* __restrict__ mask,
+                                const cx<T>* __restrict__ sigma, double s1re, double s1im, int d, int64_t N,
+                                double inv_ne2, cx<T>* __restrict__ grad, double* __restrict__ partials) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)VEC_THREADS + threadIdx.x; i < N; i += (int64_t)gridDim.x * VEC_THREADS) {
+        double gr = 0.0, gi = 0.0;
+        for (int c = 0; c < d; ++c) {
+            const double er = (double)E[c * N + i].x, ei = (double)E[c * N + i].y;
+            gr += er * er - ei * ei;
+            gi += 2.0 * er * ei;
+        }
+        if (grad) grad[i] = mkc((T)(gr * inv_ne2), (T)(gi * inv_ne2));
+        double sr, si;
+        if (sigma) {
+            sr = (double)sigma[i].x;
+            si = (double)sigma[i].y;
+        } else {
+            const bool inc = mask[i] != 0;
+            sr = inc ? s1re : 1.0;
+            si = inc ? s1im : 0.0;
+        }
+        if (mask[i]) {
+            acc[0] += gr;
+            acc[1] += gi;
+        }
+        acc[2] += sr * gr - si * gi;
+        acc[3] += sr * gi + si * gr;
+    }
+    __shared__ double red[VEC_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = 0; v < 4; ++v) {
+        double x = acc[v];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int w = 0; w < VEC_THREADS / 32; ++w) s += red[w][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = s;
+    }
+}
+
+template <typename T>
+__global__ void convert_field_kernel(cx<T>* __restrict__ dst, const double2* __restrict__ src, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = mkc((T)src[i].x, (T)src[i].y);
+}
+
+template <typename T>
+cudaError_t launch_gradient(const cx<T>* E, const uint8_t* mask, const cx<T>* sigma, double s1re, double s1im, int d,
+                            int64_t N, double inv_ne2, cx<T>* grad, int blocks, double* partials, cudaStream_t s) {
+    gradient_kernel<T><<<blocks, VEC_THREADS, 0, s>>>(E, mask, sigma, s1re, s1im, d, N, inv_ne2, grad, partials);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_convert_field(cx<T>* dst, const double2* src, int64_t N, int sm_count, cudaStream_t s) {
+    convert_field_kernel<T><<<sm_count * 8, 256, 0, s>>>(dst, src, N);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_gradient<float>(const cx<float>*, const uint8_t*, const cx<float>*, double, double, int,
+                                            int64_t, double, cx<float>*, int, double*, cudaStream_t);
+template cudaError_t launch_gradient<double>(const cx<double>*, const uint8_t*, const cx<double>*, double, double, int,
+                                             int64_t, double, cx<double>*, int, double*, cudaStream_t);
+template cudaError_t launch_convert_field<float>(cx<float>*, const double2*, int64_t, int, cudaStream_t);
+template cudaError_t launch_convert_field<double>(cx<double>*, const double2*, int64_t, int, cudaStream_t);
 
 }  // namespace lsfft

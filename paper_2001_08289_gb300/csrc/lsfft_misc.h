@@ -26,7 +26,7 @@ enum { OP_QUERY = 0, OP_PREPARE = 1, OP_LAUNCH = 2 };
 
 template <typename T>
 cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams& prm, int64_t Ntot,
-                        int d, int packed, int sm_count, cudaStream_t s);
+                        int d, int packed, const cx<T>* sigma, int sm_count, cudaStream_t s);
 
 cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
                             double* hist, int final_mode, cudaStream_t s);
@@ -47,4 +47,28 @@ template <> cudaError_t col_dispatch<float, 2>(int, int, const PassArgs<float>*,
 template <> cudaError_t col_dispatch<float, 3>(int, int, const PassArgs<float>*, cudaStream_t, Geom*);
 template <> cudaError_t col_dispatch<double, 2>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
 template <> cudaError_t col_dispatch<double, 3>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
+}  // namespace lsfft
+
+namespace lsfft {
+// Lanczos vector kernels (lsfft_misc.cu); `out` receives one FP64 scalar.
+template <typename T>
+cudaError_t lanczos_init(cx<T>* v, const uint8_t* mask, int64_t N, int d, const double* e, int blocks,
+                         double* partials, double* out, cudaStream_t s);
+template <typename T>
+cudaError_t lanczos_dot(const cx<T>* a, const cx<T>* b, int64_t L, int blocks, double* partials, double* out,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t lanczos_axpy_norm(cx<T>* w, const cx<T>* v, const cx<T>* u, double alpha, double beta, int64_t L,
+                              int blocks, double* partials, double* out, cudaStream_t s);
+template <typename T>
+cudaError_t lanczos_scale(cx<T>* dst, const cx<T>* src, double sc, int64_t L, int blocks, cudaStream_t s);
+}  // namespace lsfft
+
+namespace lsfft {
+// Gradient of sigma_* and conversion of the per-voxel conductivity (lsfft_misc.cu).
+template <typename T>
+cudaError_t launch_gradient(const cx<T>* E, const uint8_t* mask, const cx<T>* sigma, double s1re, double s1im, int d,
+                            int64_t N, double inv_ne2, cx<T>* grad, int blocks, double* partials, cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert_field(cx<T>* dst, const double2* src, int64_t N, int sm_count, cudaStream_t s);
 }  // namespace lsfft

@@ -8,7 +8,7 @@
 
 namespace lsfft {
 
-enum { SCHEME_MS = 0, SCHEME_EM = 1, SCHEME_MS_SUB = 2, SCHEME_EM_SUB = 3 };
+enum { SCHEME_MS = 0, SCHEME_EM = 1, SCHEME_MS_SUB = 2, SCHEME_EM_SUB = 3, SCHEME_MATVEC = 4 };
 enum { GREEN_TRIG = 0, GREEN_FD = 1 };
 enum { MODE_ROW_FIRST = 0, MODE_ROW_ITER = 1, MODE_ROW_OUTPUT = 2 };
 enum { MODE_COL_FWD = 0, MODE_COL_INV = 1, MODE_COL_GAMMA = 2 };
@@ -34,6 +34,8 @@ struct SchemeParams {
     double g_a[2], g_b[2], g_a0[2], g_ce[2];
     // initial state: Q = (phase 1 ? iq_in : iq_out) e, S = is_in e, T = it_in e on phase 1
     double iq_in[2], iq_out[2], is_in[2], it_in[2];
+    // per-voxel conductivity mode (MS / EM only): reference medium sigma_0 and 1/sigma_0
+    double s0[2], inv_s0[2];
 };
 
 struct Ctrl {

@@ -58,3 +58,21 @@ def test_create_grid_rejects_bad_shapes_before_touching_cuda(lib):
         with pytest.raises(L.LsfftError) as ei:
             L.lsfft_create_grid(d, n, np.zeros(int(np.prod(n)), np.uint8))
         assert ei.value.status == L.EINVAL
+
+
+def test_tridiag_gauss_matches_dense_eigh(lib):
+    """The host Gauss-quadrature helper against numpy's symmetric eigensolver."""
+    import paper_2001_08289_gb300 as L
+
+    L.load_library()
+    rng = np.random.default_rng(0)
+    for m in (1, 2, 5, 40, 120):
+        a = rng.uniform(0.0, 1.0, m)
+        b = rng.uniform(0.05, 0.5, max(m - 1, 0))
+        T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+        w, V = np.linalg.eigh(T)
+        nodes, first2 = L.lsfft_tridiag_gauss(a, b)
+        order = np.argsort(nodes)
+        np.testing.assert_allclose(nodes[order], w, atol=1e-12)
+        np.testing.assert_allclose(first2[order], V[0] ** 2, atol=1e-10)
+        assert abs(first2.sum() - 1.0) < 1e-12
