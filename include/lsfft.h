@@ -148,6 +148,24 @@ int lsfft_copy_field(const lsfft_result *res, void *dst, int dst_on_device);
 /* Free the result's host history and device field. */
 void lsfft_free_result(lsfft_result *res);
 
+/* One solve of a batch: grid, sigma_1, applied field (d entries used), options. */
+typedef struct {
+    lsfft_grid *grid;
+    lsfft_c128 sigma1;
+    double e[3];
+    lsfft_opts opts;
+} lsfft_job;
+
+/* Run many solves: jobs that share a grid run in their order on that grid's
+ * stream, jobs on different grids run concurrently (one solve in flight per
+ * grid, driven by a host scheduler that polls CUDA events instead of
+ * blocking), e.g. a sweep of sigma_1 over microstructures of different sizes.
+ * results[j] / statuses[j] receive what lsfft_solve would return for job j
+ * (a result for OK, ENOTCONV, EDIVERGED; NULL otherwise).  The call returns
+ * LSFFT_OK once every job has finished, or EINVAL (with nothing run) for null
+ * arrays or a job without grid.  Grids must not be used elsewhere meanwhile. */
+int lsfft_solve_batch(int njobs, const lsfft_job *jobs, lsfft_result **results, int *statuses);
+
 /* Per-voxel conductivity sigma(x) (complex, N entries, host or device
  * pointer; copied).  Subsequent solves on the grid use sigma(x) instead of the
  * two-phase 1 + (sigma_1 - 1) chi(x) of the mask, with the MS or EM scheme only

@@ -27,7 +27,8 @@ __all__ = [
     "lsfft_version", "lsfft_last_error", "lsfft_strerror", "lsfft_create_grid", "lsfft_create_grid_device",
     "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
     "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
-    "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "make_opts",
+    "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "lsfft_solve_batch", "solve_batch",
+    "make_opts",
     "SCHEMES", "GREENS",
 ]
 
@@ -60,6 +61,11 @@ class Opts(C.Structure):
     _fields_ = [("scheme", C.c_int), ("precision", C.c_int), ("green", C.c_int), ("max_iter", C.c_int),
                 ("stop_consecutive", C.c_int), ("check_every", C.c_int), ("tol", C.c_double),
                 ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class _Job(C.Structure):
+    """Mirror of lsfft_job."""
+    _fields_ = [("grid", C.c_void_p), ("sigma1", _C128), ("e", C.c_double * 3), ("opts", Opts)]
 
 
 class _Result(C.Structure):
@@ -111,6 +117,7 @@ def load_library():
     lib.lsfft_tridiag_gauss.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.lsfft_set_sigma_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int, _C128]
+    lib.lsfft_solve_batch.argtypes = [C.c_int, C.POINTER(_Job), C.POINTER(C.POINTER(_Result)), C.POINTER(C.c_int)]
     lib.lsfft_gradient.argtypes = [C.c_void_p, C.POINTER(_Result), C.POINTER(C.c_double), C.c_void_p,
                                    C.POINTER(_C128), C.POINTER(_C128)]
     _lib = lib
@@ -232,6 +239,32 @@ def lsfft_lanczos_hull(grid: int, e, green="trig", precision="fp32", steps: int 
     _check(load_library().lsfft_lanczos_hull(C.c_void_p(grid), ev, g, pr, int(steps), float(cutoff), C.byref(al),
                                              C.byref(be), p(nodes), p(weights), C.byref(m)))
     return al.value, be.value, nodes[:m.value].copy(), weights[:m.value].copy()
+
+
+def lsfft_solve_batch(jobs):
+    """jobs: list of (grid handle, sigma1, e, Opts).  Returns [(status, result pointer or None)]."""
+    n = len(jobs)
+    arr = (_Job * max(n, 1))()
+    for i, (h, s1, e, o) in enumerate(jobs):
+        s1 = complex(s1)
+        arr[i].grid = h
+        arr[i].sigma1 = _C128(s1.real, s1.imag)
+        ev = list(e) + [0.0] * (3 - len(e))
+        for c in range(3):
+            arr[i].e[c] = float(ev[c])
+        arr[i].opts = o
+    res = (C.POINTER(_Result) * max(n, 1))()
+    st = (C.c_int * max(n, 1))()
+    _check(load_library().lsfft_solve_batch(n, arr, res, st))
+    return [(st[i], res[i] if res[i] else None) for i in range(n)]
+
+
+def solve_batch(jobs):
+    """jobs: list of (Grid, sigma1, e, kwargs for make_opts).  Returns [Result or LsfftError]."""
+    out = []
+    for st, ptr in lsfft_solve_batch([(g.handle, s1, e, make_opts(**kw)) for g, s1, e, kw in jobs]):
+        out.append(Result(st, ptr) if ptr else LsfftError(st, lsfft_strerror(st)))
+    return out
 
 
 def lsfft_set_sigma_field(grid: int, sigma_ptr, on_device: bool, sigma0: complex = 0.0) -> None:

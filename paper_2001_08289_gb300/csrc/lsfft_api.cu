@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <cmath>
 #include <complex>
 #include <map>
@@ -89,6 +90,17 @@ struct lsfft_grid {
     void* fd[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // FD symbol per axis, FP32/FP64
     bool prepared[2] = {false, false};
     int packed = 0;                 // packed real layout for the current solve
+    // solve in flight (begin_solve / poll_solve)
+    int phase = 0;                  // 0 idle, 1 in flight
+    bool phase_finish = false;      // the output pass has been enqueued
+    cudaGraphExec_t cur_exec = nullptr;
+    int cur_st = 0, cur_nblocks = 0, cur_per_iter = 0, cur_check_every = 0;
+    int64_t cur_launches = 0, cur_max_launches = 0, cur_kernels = 0;
+    void* cur_E = nullptr;
+    lsfft_result* cur_res = nullptr;
+    double* hist_host = nullptr;    // pinned copy of the history
+    int hist_host_cap = 0;
+    cudaEvent_t ev_check = nullptr;
     // per-voxel conductivity mode (lsfft_set_sigma_field)
     double2* sigma64 = nullptr;     // device copy, FP64 complex [N]
     void* sigma_t = nullptr;        // the same in the precision of the last solve
@@ -285,6 +297,7 @@ int create_common(int d, const int64_t n[3], const uint8_t* mask, bool on_device
     if (e == cudaSuccess) e = cudaMallocHost(&g->ctrl_host, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_check, cudaEventDisableTiming);
     if (e != cudaSuccess) rc = fail_cuda(e, "create_grid");
     if (rc == LSFFT_OK) rc = build_tables(g);
     if (rc == LSFFT_OK) {
@@ -637,90 +650,147 @@ int start_solve(lsfft_grid* g, int st) {
     return LSFFT_OK;
 }
 
+// Drop a solve that failed: wait for its work and release its output buffer.
+void abandon_solve(lsfft_grid* g) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    if (g->cur_E) cudaFree(g->cur_E);
+    g->cur_E = nullptr;
+    g->phase = 0;
+    g->phase_finish = false;
+}
+
+// A solve is a small state machine so that lsfft_solve_batch can keep one
+// solve in flight per grid without blocking: begin_solve enqueues the start and
+// the first stop check; poll_solve advances on completed events (another graph
+// chunk, or the output pass once the device reported `done`) and fills the
+// result when the output has landed.
 template <typename T>
-int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
+int begin_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     int rc = ensure_prepared<T>(g);   // shared-memory limits must be set before capture
     if (rc != LSFFT_OK) return rc;
     rc = prepare_sigma<T>(g);         // the captured kernels point at the converted field
     if (rc != LSFFT_OK) return rc;
     const int nblocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
-    cudaGraphExec_t exec;
-    rc = get_graph<T>(g, st, nblocks, o->check_every, &exec);
+    rc = get_graph<T>(g, st, nblocks, o->check_every, &g->cur_exec);
     if (rc != LSFFT_OK) return rc;
     rc = start_solve<T>(g, st);
     if (rc != LSFFT_OK) return rc;
-    // Every finalize either sets `done` or advances the iteration count, so the
-    // loop ends after at most max_iter / check_every + 1 graph launches; the
-    // bound below only guards against kernels that silently did not run.
-    const int64_t max_launches = (int64_t)o->max_iter / o->check_every + 2;
-    const int per_iter = g->d == 2 ? 3 : 5;   // row pass, finalize, strided pass(es)
-    int64_t kernels = 1 + per_iter;           // init + first update
-    for (int64_t launches = 0;; ++launches) {
-        CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
-        CK(cudaStreamSynchronize(g->stream));
-        if (g->ctrl_host->done) break;
-        if (launches > max_launches) {
-            g_last_error = "iteration control block never reported completion";
-            return LSFFT_ECUDA;
-        }
-        CK(cudaGraphLaunch(exec, g->stream));
-        kernels += (int64_t)per_iter * o->check_every;
+    if (g->hist_host_cap < g->hist_cap) {
+        if (g->hist_host) cudaFreeHost(g->hist_host);
+        g->hist_host = nullptr;
+        g->hist_host_cap = 0;
+        CK(cudaMallocHost(&g->hist_host, sizeof(double) * HIST_STRIDE * g->hist_cap));
+        g->hist_host_cap = g->hist_cap;
     }
-    kernels += 2;                             // output row pass and final finalize
-    const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
-    void* E = nullptr;
-    CK(cudaMallocAsync(&E, ebytes, g->stream));
-    cudaError_t e = launch_row<T>(g, st, MODE_ROW_OUTPUT, (cx<T>*)E);
-    if (e == cudaSuccess)
-        e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1, g->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(g->ev1, g->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    if (e != cudaSuccess) {
-        cudaFreeAsync(E, g->stream);
-        return fail_cuda(e, "solve");
-    }
-    const Ctrl& C = *g->ctrl_host;
-    res->E_device = E;
-    res->iters = C.iter;
-    res->status = C.status;
-    res->hist_len = C.iter + 1;
-    res->sigma_star.re = C.sigma[0];
-    res->sigma_star.im = C.sigma[1];
-    for (int c = 0; c < g->d; ++c) {
-        res->mean_E[c].re = C.meanE[c][0];
-        res->mean_E[c].im = C.meanE[c][1];
-        res->mean_J[c].re = C.meanJ[c][0];
-        res->mean_J[c].im = C.meanJ[c][1];
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, g->ev0, g->ev1);
-    res->solve_ms = ms;
-    res->kernel_launches = kernels;
-    res->packed = g->packed;
-    const int L = res->hist_len;
-    double* h = (double*)malloc(sizeof(double) * HIST_STRIDE * L);
-    res->hist_sigma_re = (double*)malloc(sizeof(double) * L);
-    res->hist_sigma_im = (double*)malloc(sizeof(double) * L);
-    res->hist_rel_change = (double*)malloc(sizeof(double) * L);
-    res->hist_field_norm = (double*)malloc(sizeof(double) * L);
-    if (!h || !res->hist_sigma_re || !res->hist_sigma_im || !res->hist_rel_change || !res->hist_field_norm) {
-        free(h);
-        return LSFFT_ENOMEM;
-    }
-    e = cudaMemcpy(h, g->hist, sizeof(double) * HIST_STRIDE * L, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-        free(h);
-        return fail_cuda(e, "history download");
-    }
-    for (int k = 0; k < L; ++k) {
-        res->hist_sigma_re[k] = h[HIST_STRIDE * k + 0];
-        res->hist_sigma_im[k] = h[HIST_STRIDE * k + 1];
-        res->hist_rel_change[k] = h[HIST_STRIDE * k + 2];
-        res->hist_field_norm[k] = h[HIST_STRIDE * k + 3];
-    }
-    free(h);
+    // Every finalize either sets `done` or advances the iteration count, so at
+    // most max_iter / check_every + 1 graph launches are needed; the bound only
+    // guards against kernels that silently did not run.
+    g->cur_max_launches = (int64_t)o->max_iter / o->check_every + 2;
+    g->cur_launches = 0;
+    g->cur_per_iter = g->d == 2 ? 3 : 5;      // row pass, finalize, strided pass(es)
+    g->cur_kernels = 1 + g->cur_per_iter;     // init + first update
+    g->cur_check_every = o->check_every;
+    g->cur_st = st;
+    g->cur_nblocks = nblocks;
+    g->cur_E = nullptr;
+    g->cur_res = res;
+    CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaEventRecord(g->ev_check, g->stream));
+    g->phase = 1;
     return LSFFT_OK;
+}
+
+// Returns 0 while the solve is in flight, 1 once the result is filled, or an
+// error status (the solve is then abandoned).
+template <typename T>
+int poll_solve(lsfft_grid* g) {
+    const cudaError_t q = cudaEventQuery(g->ev_check);
+    if (q == cudaErrorNotReady) return 0;
+    g->phase = 0;
+    if (q != cudaSuccess) return fail_cuda(q, "solve");
+    lsfft_result* res = g->cur_res;
+    if (g->phase_finish) {
+        g->phase_finish = false;
+        const Ctrl& C = *g->ctrl_host;
+        res->E_device = g->cur_E;
+        g->cur_E = nullptr;
+        res->iters = C.iter;
+        res->status = C.status;
+        res->hist_len = C.iter + 1;
+        res->sigma_star.re = C.sigma[0];
+        res->sigma_star.im = C.sigma[1];
+        for (int c = 0; c < g->d; ++c) {
+            res->mean_E[c].re = C.meanE[c][0];
+            res->mean_E[c].im = C.meanE[c][1];
+            res->mean_J[c].re = C.meanJ[c][0];
+            res->mean_J[c].im = C.meanJ[c][1];
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, g->ev0, g->ev1);
+        res->solve_ms = ms;
+        res->kernel_launches = g->cur_kernels;
+        res->packed = g->packed;
+        const int L = res->hist_len;
+        res->hist_sigma_re = (double*)malloc(sizeof(double) * L);
+        res->hist_sigma_im = (double*)malloc(sizeof(double) * L);
+        res->hist_rel_change = (double*)malloc(sizeof(double) * L);
+        res->hist_field_norm = (double*)malloc(sizeof(double) * L);
+        if (!res->hist_sigma_re || !res->hist_sigma_im || !res->hist_rel_change || !res->hist_field_norm)
+            return LSFFT_ENOMEM;
+        const double* h = g->hist_host;
+        for (int k = 0; k < L; ++k) {
+            res->hist_sigma_re[k] = h[HIST_STRIDE * k + 0];
+            res->hist_sigma_im[k] = h[HIST_STRIDE * k + 1];
+            res->hist_rel_change[k] = h[HIST_STRIDE * k + 2];
+            res->hist_field_norm[k] = h[HIST_STRIDE * k + 3];
+        }
+        return 1;
+    }
+    if (g->ctrl_host->done) {
+        // output pass: E of the last iterate, its sigma_* and averages, history
+        g->cur_kernels += 2;
+        const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
+        CK(cudaMallocAsync(&g->cur_E, ebytes, g->stream));
+        CK(launch_row<T>(g, g->cur_st, MODE_ROW_OUTPUT, (cx<T>*)g->cur_E));
+        CK(launch_finalize(g->partials, g->cur_nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1,
+                           g->stream));
+        CK(cudaEventRecord(g->ev1, g->stream));
+        CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+        const int L = g->ctrl_host->iter + 1;
+        CK(cudaMemcpyAsync(g->hist_host, g->hist, sizeof(double) * HIST_STRIDE * L, cudaMemcpyDeviceToHost,
+                           g->stream));
+        CK(cudaEventRecord(g->ev_check, g->stream));
+        g->phase_finish = true;
+        g->phase = 1;
+        return 0;
+    }
+    if (g->cur_launches++ > g->cur_max_launches) {
+        g_last_error = "iteration control block never reported completion";
+        return LSFFT_ECUDA;
+    }
+    CK(cudaGraphLaunch(g->cur_exec, g->stream));
+    g->cur_kernels += (int64_t)g->cur_per_iter * g->cur_check_every;
+    CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaEventRecord(g->ev_check, g->stream));
+    g->phase = 1;
+    return 0;
+}
+
+template <typename T>
+int run_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
+    int rc = begin_solve<T>(g, o, st, res);
+    while (rc == LSFFT_OK) {
+        const int p = poll_solve<T>(g);
+        if (p == 1) return LSFFT_OK;
+        if (p != 0) {
+            rc = p;
+            break;
+        }
+        cudaEventSynchronize(g->ev_check);
+    }
+    abandon_solve(g);
+    return rc;
 }
 
 }  // namespace
@@ -771,6 +841,9 @@ void lsfft_destroy_grid(lsfft_grid* g) {
     }
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->ev_check) cudaEventDestroy(g->ev_check);
+    if (g->hist_host) cudaFreeHost(g->hist_host);
+    if (g->cur_E) cudaFree(g->cur_E);
     cudaFree(g->sigma64);
     cudaFree(g->sigma_t);
     if (g->own_stream) cudaStreamDestroy(g->stream);
@@ -1252,6 +1325,90 @@ int lsfft_gradient(lsfft_grid* g, const lsfft_result* res, const double* e, void
     }
     return res->precision == LSFFT_FP32 ? gradient_impl<float>(g, res, e, grad_device, dsigma1, energy)
                                         : gradient_impl<double>(g, res, e, grad_device, dsigma1, energy);
+}
+
+int lsfft_solve_batch(int njobs, const lsfft_job* jobs, lsfft_result** results, int* statuses) {
+    if (njobs < 0 || (njobs > 0 && (!jobs || !results || !statuses))) {
+        g_last_error = "lsfft_solve_batch: bad arguments";
+        return LSFFT_EINVAL;
+    }
+    for (int j = 0; j < njobs; ++j) {
+        results[j] = nullptr;
+        statuses[j] = LSFFT_EINVAL;
+        if (!jobs[j].grid) {
+            g_last_error = "lsfft_solve_batch: job without grid";
+            return LSFFT_EINVAL;
+        }
+    }
+    // jobs of one grid run in order on its stream; different grids run concurrently
+    std::vector<lsfft_grid*> grids;
+    std::map<lsfft_grid*, std::vector<int>> queue;
+    for (int j = 0; j < njobs; ++j) {
+        if (!queue.count(jobs[j].grid)) grids.push_back(jobs[j].grid);
+        queue[jobs[j].grid].push_back(j);
+    }
+    std::map<lsfft_grid*, size_t> next;
+    std::map<lsfft_grid*, int> cur, cur_prec;
+    for (auto* g : grids) {
+        next[g] = 0;
+        cur[g] = -1;
+    }
+    int remaining = njobs;
+    while (remaining > 0) {
+        bool progress = false;
+        for (auto* g : grids) {
+            const int j = cur[g];
+            if (j < 0) {
+                if (next[g] >= queue[g].size()) continue;
+                const int k = queue[g][next[g]++];
+                progress = true;
+                const lsfft_job& J = jobs[k];
+                int st = 0;
+                int rc = check_and_setup(g, J.sigma1, J.e, &J.opts, &st);
+                lsfft_result* res = nullptr;
+                if (rc == LSFFT_OK) {
+                    res = (lsfft_result*)calloc(1, sizeof(lsfft_result));
+                    if (!res) rc = LSFFT_ENOMEM;
+                }
+                if (rc == LSFFT_OK) {
+                    res->precision = J.opts.precision;
+                    res->sigma1 = J.sigma1;
+                    res->d = g->d;
+                    for (int a = 0; a < 3; ++a) res->n[a] = a < g->d ? g->n[a] : 1;
+                    rc = J.opts.precision == LSFFT_FP32 ? begin_solve<float>(g, &J.opts, st, res)
+                                                        : begin_solve<double>(g, &J.opts, st, res);
+                    if (rc != LSFFT_OK) {
+                        abandon_solve(g);
+                        lsfft_free_result(res);
+                    }
+                }
+                if (rc != LSFFT_OK) {
+                    statuses[k] = rc;
+                    --remaining;
+                    continue;
+                }
+                cur[g] = k;
+                cur_prec[g] = J.opts.precision;
+                continue;
+            }
+            const int p = cur_prec[g] == LSFFT_FP32 ? poll_solve<float>(g) : poll_solve<double>(g);
+            if (p == 0) continue;
+            progress = true;
+            lsfft_result* res = g->cur_res;
+            if (p == 1) {
+                results[j] = res;
+                statuses[j] = res->status == ST_OK ? LSFFT_OK : res->status;
+            } else {
+                abandon_solve(g);
+                lsfft_free_result(res);
+                statuses[j] = p;
+            }
+            cur[g] = -1;
+            --remaining;
+        }
+        if (!progress) std::this_thread::yield();
+    }
+    return LSFFT_OK;
 }
 
 }  // extern "C"
