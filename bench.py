@@ -39,6 +39,10 @@ SCHEMES = ("ms", "em_sub")
 ALPHA_BETA = (0.25, 4.0)          # the Moulinec-Suquet estimate quoted in the paper
 TOL = 1e-6
 FRACTION = 0.25
+# Lanczos extreme nodes lie inside the weighted spectrum, so the estimated slit
+# is a little short; widening it only slows convergence slightly (section
+# "Estimating the parameters alpha and beta"), a short one can diverge.
+HULL_MARGIN = 0.05
 
 
 def parse():
@@ -53,6 +57,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--pass-reps", type=int, default=20)
+    p.add_argument("--workload", default="square2d",
+                   choices=("square2d", "lattice64", "cube3d", "sweep", "adjoint"),
+                   help="square2d (default): the headline 2-D square-array sweep; the others measure the "
+                        "64^2 FP64 lattice, the 3-D cubic arrays, the batched complex-sigma_1 sweep and the "
+                        "adjoint (gradient) configuration, one JSON line each")
+    p.add_argument("--sweep-sigmas", type=int, default=16, help="sweep: sigma_1 values per microstructure per step")
+    p.add_argument("--fd-voxels", type=int, default=16, help="adjoint: voxels checked by central differences")
     return p.parse_args()
 
 
@@ -378,13 +389,254 @@ def run_ours(args, sigmas):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# further workloads (one JSON line each; not the driver's default)
+# ---------------------------------------------------------------------------
+def _gpu_setup():
+    import torch
+
+    import paper_2001_08289_gb300 as L
+    from paper_2001_08289_gb300 import build
+
+    torch.cuda.set_device(0)
+    build.build()
+    L.load_library()
+    return torch, L
+
+
+def _line(metric, value, unit, args, config, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "workload_kind": args.workload, "config": config}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_lattice64(args):
+    """64^2 square array, sigma_1 = 10, FP64, stop at relative change 1e-10: microseconds
+    per iteration and iterations per scheme (latency-bound: not a roofline case)."""
+    torch, L = _gpu_setup()
+    mask = square_array_mask(64)
+    e = [1.0, 0.0]
+    out = {}
+    with L.Grid(mask) as g:
+        hulls = {}
+        for green, cut in (("trig", 1e-3), ("fd", 1e-10)):
+            a, b, _, _ = g.lanczos_hull(e, green=green, precision="fp64", steps=200, cutoff=cut)
+            hulls[green] = (a, b)
+        for green in ("trig", "fd"):
+            a, b = hulls[green]
+            for sch in ("ms", "em", "ms_sub", "em_sub"):
+                kw = dict(scheme=sch, precision="fp64", green=green, tol=1e-10, max_iter=2000, alpha=a, beta=b)
+                for _ in range(args.warmup):
+                    g.solve(10.0, e, **kw).free()
+                ms, its = [], []
+                for _ in range(args.steps):
+                    r = g.solve(10.0, e, **kw)
+                    ms.append(r.solve_ms)
+                    its.append(r.iterations)
+                    sig = r.sigma_star
+                    r.free()
+                out[f"{green}|{sch}"] = {"iters": its[-1], "solve_ms": round(float(np.median(ms)), 4),
+                                         "us_per_iter": round(1e3 * float(np.median(ms)) / its[-1], 2),
+                                         "sigma_star": sig.real}
+    tot_vox = sum(v["iters"] for v in out.values()) * mask.size
+    tot_s = sum(v["solve_ms"] for v in out.values()) / 1e3
+    _line("voxel-iters/s (64^2 FP64 lattice)", tot_vox / tot_s, UNIT, args,
+          {"workload": "64x64 square array, sigma1=10, FP64, stop 1e-10, alpha/beta from GPU Lanczos "
+                       "(trig: cutoff 1e-3, fd: cutoff 1e-10)", "hulls": hulls},
+          dtype="c128", per_scheme=out)
+
+
+def run_cube3d(args):
+    """3-D cubic array of cubes of side n/2 (f = 1/8), sigma_1 in {5, 50, 500}, FP32,
+    MS vs EM in H'' with alpha, beta from GPU Lanczos: voxel-iters/s and pass roofline."""
+    from synth import SIGMA1_SWEEP_3D
+
+    torch, L = _gpu_setup()
+    n = args.n if args.n <= 512 else 256
+    mask = square_array_mask(n, d=3)
+    N = mask.size
+    e = [1.0, 0.0, 0.0]
+    stream = torch.cuda.Stream()
+    per = {}
+    # The forward-difference symbol: its weighted poles fill a clean interval, as the
+    # substitution assumes; the trigonometric symbol has tiny-weight poles far outside
+    # any truncated hull, on which EM in H'' diverges for large sigma_1 (the oracle
+    # shows the same).
+    green = "fd"
+    with L.Grid(mask, stream=stream.cuda_stream) as g:
+        a, b, _, _ = g.lanczos_hull(e, green=green, precision="fp32", steps=60, cutoff=1e-8)
+        a, b = a * (1 - HULL_MARGIN), b * (1 + HULL_MARGIN)
+        kws = {sch: dict(scheme=sch, precision="fp32", green=green, tol=TOL, max_iter=400, alpha=a, beta=b)
+               for sch in SCHEMES}
+        for _ in range(args.warmup):
+            for s1 in SIGMA1_SWEEP_3D:
+                for sch in SCHEMES:
+                    g.solve(s1, e, **kws[sch]).free()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        vox = 0
+        for _ in range(args.steps):
+            for s1 in SIGMA1_SWEEP_3D:
+                for sch in SCHEMES:
+                    r = g.solve(s1, e, **kws[sch])
+                    vox += r.iterations * N
+                    per.setdefault(str(s1), {})[sch] = {"iters": r.iterations, "status": r.status,
+                                                        "ms": round(r.solve_ms, 3), "sigma_star": r.sigma_star.real}
+                    r.free()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        peak, _ = measured_peaks()
+        passes = {}
+        for sch in SCHEMES:
+            g.prepare(50.0, e, **dict(kws[sch], tol=0.0, max_iter=100000))
+            for kind, name, nbytes in ((0, "row", N * (2 * 24 + 1 + (4 * 24 * 0.125 if sch == "em_sub" else 0))),
+                                       (1, "strided_x3", 3 * N * 2 * 24)):
+                with torch.cuda.stream(stream):
+                    g.launch_passes(kind, 2)
+                    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    t0.record(stream)
+                    g.launch_passes(kind, args.pass_reps)
+                    t1.record(stream)
+                torch.cuda.synchronize()
+                ms = t0.elapsed_time(t1) / args.pass_reps
+                passes[f"{name}|{sch}"] = {"ms": round(ms, 4), "alg_bytes": int(nbytes),
+                                           "GBps": round(nbytes / ms / 1e6, 1),
+                                           "frac_of_measured_hbm": round(nbytes / ms / 1e6 / peak, 4)}
+    _line(METRIC, vox / elapsed, UNIT, args,
+          {"workload": f"3D cubic array of cubes (f=1/8), {n}^3, sigma1 in {list(SIGMA1_SWEEP_3D)}, MS vs "
+                       f"EM-in-H'' with Lanczos (alpha,beta)=({a:.4g},{b:.4g}) widened by {HULL_MARGIN:g}, "
+                       f"tol {TOL:g}, fd Green symbol",
+           "n": n, "d": 3}, dtype="c64", ms_per_step=1e3 * elapsed / args.steps, time_to_tol=per, passes=passes)
+
+
+def run_sweep(args):
+    """Batched complex-sigma_1 sweep: 32 RSA-disk microstructures (n in 128..1024, 8
+    each), sigma_1 = r e^{i theta}, EM in H'' with per-microstructure Lanczos
+    alpha, beta; all solves of a step go through one lsfft_solve_batch call."""
+    from synth import complex_sigma_ray, rsa_disk_mask
+
+    torch, L = _gpu_setup()
+    sizes = [128] * 8 + [256] * 8 + [512] * 8 + [1024] * 8
+    grids, hulls, vox_n = [], [], []
+    for s, n in enumerate(sizes):
+        m, info = rsa_disk_mask(n, seed=s)
+        g = L.Grid(m)
+        a, b, _, _ = g.lanczos_hull([1.0, 0.0], green="fd", precision="fp32", steps=60, cutoff=1e-6)
+        grids.append(g)
+        hulls.append((a * (1 - HULL_MARGIN), b * (1 + HULL_MARGIN)))
+        vox_n.append(m.size)
+    allsig = complex_sigma_ray(count=512, seed=1000)
+
+    def step(k):
+        sig = allsig[(k * args.sweep_sigmas) % 512:][:args.sweep_sigmas]
+        jobs = []
+        for g, (a, b) in zip(grids, hulls):
+            for s1 in sig:
+                # EM in H'' where it is stable against rounding (rate < limit), else plain EM
+                rate, limit = L.lsfft_substitution_rates(s1, a, b)
+                sch = "em_sub" if rate < 0.98 * limit else "em"
+                jobs.append((g, s1, [1.0, 0.0], dict(scheme=sch, green="fd", tol=TOL, max_iter=400, alpha=a, beta=b)))
+        out = L.solve_batch(jobs)
+        vox = sum(r.iterations * jobs[i][0].N for i, r in enumerate(out) if not isinstance(r, Exception))
+        st = [(jobs[i][3]["scheme"], getattr(r, "status", -1)) for i, r in enumerate(out)]
+        for r in out:
+            if not isinstance(r, Exception):
+                r.free()
+        return vox, len(jobs), st
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vox = solves = 0
+    statuses = []
+    for k in range(args.steps):
+        v, nj, st = step(args.warmup + k)
+        vox += v
+        solves += nj
+        statuses += st
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for g in grids:
+        g.close()
+    _line("voxel-iters/s (batched complex-sigma1 sweep)", vox / dt, UNIT, args,
+          {"workload": f"32 RSA-disk microstructures (n=128..1024, 8 each), {args.sweep_sigmas} complex sigma1 "
+                       f"per microstructure per step from the r e^(i theta) ray (seed 1000), EM-in-H'' with "
+                       f"per-microstructure Lanczos alpha,beta (fd, cutoff 1e-6) widened by {HULL_MARGIN:g} "
+                       f"(plain EM where EM-in-H'' is not rounding-stable), tol {TOL:g}, FP32, at most 400 "
+                       f"iterations",
+           "solves_per_step": solves // max(args.steps, 1)},
+          dtype="c64", solves_per_s=solves / dt, ms_per_step=1e3 * dt / args.steps,
+          status_counts={f"{sch}:{st}": statuses.count((sch, st)) for sch, st in sorted(set(statuses))})
+
+
+def run_adjoint(args):
+    """128^3 Bernoulli(0.2) voxels after one periodic 3x3x3 majority filter,
+    sigma = 1 + 19 chi: forward solve plus gradient, and central differences
+    (step 1e-3) of the variational energy estimate at random voxels, FP64."""
+    from synth import bernoulli_majority_mask
+
+    torch, L = _gpu_setup()
+    n = 128
+    mask = bernoulli_majority_mask(n, p=0.2, seed=5)
+    sig = 1.0 + 19.0 * mask.astype(np.float64)
+    e = [1.0, 0.0, 0.0]
+    opts = dict(scheme="em", precision="fp64", green="fd", tol=1e-15, max_iter=3000)
+    rng = np.random.default_rng(6)
+    with L.Grid(mask) as g:
+        g.set_sigma_field(sig, sigma0=np.sqrt(20.0))
+        grad = torch.empty(mask.shape, dtype=torch.complex128, device="cuda")
+        times = []
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = g.solve(1.0, e, **opts)
+            d1, en = g.gradient(r, e, grad.data_ptr())
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+            its = r.iterations
+            r.free()
+        gf = grad.cpu().numpy().real
+        # voxels: half inside the (sparse) inclusions, half anywhere
+        inc = np.argwhere(mask)
+        picks = [tuple(v) for v in inc[rng.permutation(len(inc))[:args.fd_voxels // 2]]]
+        picks += [tuple(rng.integers(0, n, 3)) for _ in range(args.fd_voxels - len(picks))]
+        errs = []
+        h = 1e-3
+        for v in picks:
+            vals = []
+            for sgn in (1, -1):
+                sp = sig.copy()
+                sp[v] += sgn * h
+                g.set_sigma_field(sp, sigma0=np.sqrt(20.0))
+                rr = g.solve(1.0, e, **opts)
+                vals.append(g.gradient(rr, e)[1].real)
+                rr.free()
+            fd = (vals[0] - vals[1]) / (2 * h)
+            errs.append(abs(fd - gf[v]) / abs(gf[v]))
+    _line("forward+gradient wall time (128^3 adjoint configuration)", float(np.median(times)), "s", args,
+          {"workload": "128^3 Bernoulli(0.2) voxels (seed 5) after one periodic 3x3x3 majority filter (>=14/27), "
+                       "sigma = 1 + 19 chi, EM FP64 tol 1e-15, fd Green symbol",
+           "inclusion_fraction": float(mask.mean())}, dtype="c128", higher_is_better=False, iterations=its,
+          dsigma_dsigma1=d1.real, energy_sigma_star=en.real, fd_voxels=len(picks), fd_max_rel_err=max(errs),
+          fd_median_rel_err=float(np.median(errs)))
+
+
 def main():
     args = parse()
     sigmas = tuple(float(s) for s in args.sigmas.split(","))
     if args.impl == "reference":
         run_reference(args, sigmas)
-    else:
+    elif args.workload == "square2d":
         run_ours(args, sigmas)
+    else:
+        {"lattice64": run_lattice64, "cube3d": run_cube3d, "sweep": run_sweep, "adjoint": run_adjoint}[
+            args.workload](args)
 
 
 if __name__ == "__main__":

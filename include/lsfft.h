@@ -75,7 +75,8 @@ typedef struct {
                               the scalar recurrence are FP64 in both                        */
     int green;             /* lsfft_green                                                   */
     int max_iter;          /* maximum number of updates, >= 1                               */
-    int stop_consecutive;  /* K >= 1: stop once K successive relative sigma_* changes < tol */
+    int stop_consecutive;  /* K >= 1: stop once, K times in a row, both the relative change
+                              of sigma_* and that of <|E|^2> are below tol                 */
     int check_every;       /* updates per CUDA-graph launch between host checks, >= 1       */
     double tol;            /* relative sigma_* change threshold (0 = run max_iter updates)  */
     double alpha, beta;    /* pole interval [-beta,-alpha], 0 < alpha < beta; *_SUB only    */
@@ -147,6 +148,18 @@ int lsfft_copy_field(const lsfft_result *res, void *dst, int dst_on_device);
 
 /* Free the result's host history and device field. */
 void lsfft_free_result(lsfft_result *res);
+
+/* Convergence and stability of EM in H'' (Eq. J4, J43, J46) for sigma_1 and
+ * [alpha, beta]: rate = |z| with z = (sqrt t - 1)/(sqrt t + 1), t = t(sigma_1) of
+ * Eq. J3; limit = min(|z(t(0))|, |z(t(inf))|).  chi Gamma_1 chi always has the
+ * eigenvalues 1 and 0 (poles at sigma_1 = 0 and -inf) on modes that carry no
+ * weight for sigma_* but are excited by rounding; in H'' they sit at t(0) and
+ * t(inf), so when rate > limit the iteration amplifies rounding noise by
+ * rate/limit per step and the field diverges although sigma_* converges.  For
+ * real sigma_1 > 0, rate < limit always; complex sigma_1 close to the slit can
+ * violate it, and plain EM is then the safe choice.  EINVAL unless
+ * 0 < alpha < beta < inf. */
+int lsfft_substitution_rates(lsfft_c128 sigma1, double alpha, double beta, double *rate, double *limit);
 
 /* One solve of a batch: grid, sigma_1, applied field (d entries used), options. */
 typedef struct {

@@ -32,10 +32,13 @@ chi'' = (p p^T) chi (x) I_d (Eq. J36, J37), projection Gamma_1''(Q, S, T) =
 By Eq. J39-J42 the Q component of the converged E'' is the physical E and
 sigma_* is unchanged.
 
-Stop rule (the paper gives none; reading): r_k = |sigma_k - sigma_{k-1}|/|sigma_k|;
-the iteration stops at the first k with r_k < tol for `consecutive` successive
-k.  The update is then applied once more and the returned field, sigma_* and
-last history entry belong to that final iterate.  A non-finite sigma_k or
+Stop rule (the paper gives none; reading): r_k = |sigma_k - sigma_{k-1}|/|sigma_k|
+and n_k = |<|E_k|^2> - <|E_{k-1}|^2>| / <|E_k|^2>; the iteration stops at the
+first k with r_k < tol and n_k < tol for `consecutive` successive k (the field
+must settle as well as sigma_*: the paper stresses that the fields are the
+real interest, and a growing field component can leave sigma_* unchanged).
+The update is then applied once more and the returned field, sigma_* and last
+history entry belong to that final iterate.  A non-finite sigma_k or
 <|E|^2>, or <|E|^2> above 1e12 times its first value, stops the run as
 diverged (again after one more update); reaching max_iter updates without
 convergence is "not converged".
@@ -317,12 +320,13 @@ def solve(pb: Problem, scheme: str, alpha=None, beta=None, tol: float = 1e-10,
             states.append({kk: v.copy() for kk, v in st.items()})
         sig, mE, mJ, norm = sch.observe(st)
         rel = abs(sig - hs[-1]) / abs(sig) if (k >= 1 and sig != 0) else np.inf
+        nrel = abs(norm - hn[-1]) / norm if (k >= 1 and norm != 0) else np.inf
         hs.append(sig)
         hr.append(rel)
         hn.append(norm)
         if norm0 is None:
             norm0 = norm
-        run = run + 1 if rel < tol else 0
+        run = run + 1 if (rel < tol and nrel < tol) else 0
         diverged = (not np.isfinite(sig.real) or not np.isfinite(sig.imag) or not np.isfinite(norm)
                     or norm > DIVERGENCE_FACTOR * norm0)
         st = sch.update(st)

@@ -28,6 +28,7 @@ __all__ = [
     "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
     "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
     "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "lsfft_solve_batch", "solve_batch",
+    "lsfft_substitution_rates",
     "make_opts",
     "SCHEMES", "GREENS",
 ]
@@ -118,6 +119,8 @@ def load_library():
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.lsfft_set_sigma_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int, _C128]
     lib.lsfft_solve_batch.argtypes = [C.c_int, C.POINTER(_Job), C.POINTER(C.POINTER(_Result)), C.POINTER(C.c_int)]
+    lib.lsfft_substitution_rates.argtypes = [_C128, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                             C.POINTER(C.c_double)]
     lib.lsfft_gradient.argtypes = [C.c_void_p, C.POINTER(_Result), C.POINTER(C.c_double), C.c_void_p,
                                    C.POINTER(_C128), C.POINTER(_C128)]
     _lib = lib
@@ -239,6 +242,16 @@ def lsfft_lanczos_hull(grid: int, e, green="trig", precision="fp32", steps: int 
     _check(load_library().lsfft_lanczos_hull(C.c_void_p(grid), ev, g, pr, int(steps), float(cutoff), C.byref(al),
                                              C.byref(be), p(nodes), p(weights), C.byref(m)))
     return al.value, be.value, nodes[:m.value].copy(), weights[:m.value].copy()
+
+
+def lsfft_substitution_rates(sigma1: complex, alpha: float, beta: float):
+    """(rate, limit): EM in H'' converges at `rate` per iteration and is stable
+    against rounding only if rate < limit (see include/lsfft.h)."""
+    s1 = complex(sigma1)
+    r, lim = C.c_double(), C.c_double()
+    _check(load_library().lsfft_substitution_rates(_C128(s1.real, s1.imag), float(alpha), float(beta), C.byref(r),
+                                                   C.byref(lim)))
+    return r.value, lim.value
 
 
 def lsfft_solve_batch(jobs):

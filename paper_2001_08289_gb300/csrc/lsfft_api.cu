@@ -1411,4 +1411,22 @@ int lsfft_solve_batch(int njobs, const lsfft_job* jobs, lsfft_result** results, 
     return LSFFT_OK;
 }
 
+int lsfft_substitution_rates(lsfft_c128 sigma1, double alpha, double beta, double* rate, double* limit) {
+    if (!(alpha > 0.0 && beta > alpha && std::isfinite(beta)) || !rate || !limit) {
+        g_last_error = "lsfft_substitution_rates: need 0 < alpha < beta and output pointers";
+        return LSFFT_EINVAL;
+    }
+    auto zabs = [](cplx t) {
+        const cplx r = std::sqrt(t);
+        return std::abs((r - 1.0) / (r + 1.0));
+    };
+    const cplx s1(sigma1.re, sigma1.im);
+    const cplx t = (s1 + alpha) * (1.0 + beta) / ((s1 + beta) * (1.0 + alpha));   // Eq. J3
+    const double t0 = alpha * (1.0 + beta) / (beta * (1.0 + alpha));              // t(0)
+    const double tinf = (1.0 + beta) / (1.0 + alpha);                             // t(infinity)
+    *rate = zabs(t);
+    *limit = std::min(zabs(cplx(t0, 0.0)), zabs(cplx(tinf, 0.0)));
+    return LSFFT_OK;
+}
+
 }  // extern "C"

@@ -102,11 +102,14 @@ finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const 
         ctrl->meanJ[c][0] = tot[4 * c + 2] * P.inv_ntot;
         ctrl->meanJ[c][1] = tot[4 * c + 3] * P.inv_ntot;
     }
+    // relative change of <|E|^2>: the field must settle as well as sigma_*
+    const double nrel = (k >= 1 && norm != 0.0) ? fabs(norm - ctrl->prev_norm) / norm : INFINITY;
     ctrl->prev[0] = s_re;
     ctrl->prev[1] = s_im;
+    ctrl->prev_norm = norm;
     if (final_mode) return;
     if (k == 0) ctrl->norm0 = norm;
-    ctrl->run = (rel < P.tol) ? ctrl->run + 1 : 0;
+    ctrl->run = (rel < P.tol && nrel < P.tol) ? ctrl->run + 1 : 0;
     const bool diverged = !isfinite(s_re) || !isfinite(s_im) || !isfinite(norm) ||
                           norm > DIVERGENCE_FACTOR * ctrl->norm0;
     if (diverged) {

@@ -46,6 +46,7 @@ struct Ctrl {
     int status;      // ST_*
     int pad0, pad1, pad2;
     double prev[2];  // sigma_{k-1}
+    double prev_norm;   // <|E_{k-1}|^2>
     double norm0;    // <|E_0|^2>
     double sigma[2];
     double meanE[3][2], meanJ[3][2];

@@ -254,3 +254,33 @@ def test_per_voxel_sigma_mode_matches_full_direct_solve():
         r = S.solve(pb, scheme, tol=1e-14, max_iter=2000)
         assert abs(r.sigma_star - sf) < 1e-11
         assert np.abs(r.E - Ef).max() < 1e-9
+
+
+def test_substituted_em_rounding_stability_limit():
+    """chi Gamma chi has eigenvalues 1 and 0 on modes with no weight for sigma_*; in
+    H'' they sit at t(0) and t(inf).  Where |z(t(sigma_1))| exceeds
+    min(|z(t(0))|, |z(t(inf))|) the iteration amplifies rounding noise and the field
+    diverges although sigma_* converges; below it the field converges."""
+    import cmath
+
+    from oracle import constants as C
+    from synth import rsa_disk_mask
+
+    m, _ = rsa_disk_mask(64, seed=3)
+    mm, w = X.poles(m, E2, "fd")
+    a, b, _, _ = X.pole_hull(mm, w, 1e-10)
+    a, b = 0.9 * a, 1.1 * b
+    zabs = lambda t: abs((cmath.sqrt(t) - 1) / (cmath.sqrt(t) + 1))
+    limit = min(zabs(C.t_of_sigma1(0.0, a, b)), zabs((1 + b) / (1 + a)))
+    unstable, stable = -0.33 + 0.065j, 3.0 + 4.0j
+    assert zabs(C.t_of_sigma1(unstable, a, b)) > limit > zabs(C.t_of_sigma1(stable, a, b))
+    ru = S.solve(S.Problem(m, unstable, E2, "fd"), "em_sub", alpha=a, beta=b, tol=1e-6, max_iter=300)
+    re_ = S.solve(S.Problem(m, unstable, E2, "fd"), "em", tol=1e-6, max_iter=600)
+    rs = S.solve(S.Problem(m, stable, E2, "fd"), "em_sub", alpha=a, beta=b, tol=1e-8, max_iter=300)
+    assert re_.status == S.STATUS_OK and rs.status == S.STATUS_OK
+    # sigma_* settles to the right value while the field norm runs away: the stop
+    # rule, which watches both, never reports convergence
+    assert ru.status in (S.STATUS_DIVERGED, S.STATUS_NOTCONV)
+    k = int(np.argmax(ru.hist_field_norm > 1e3 * ru.hist_field_norm[0]))
+    assert k > 0 and abs(ru.hist_sigma[k] - re_.sigma_star) < 1e-4 * abs(re_.sigma_star)
+    assert rs.hist_field_norm.max() < 10 * rs.hist_field_norm[0]
