@@ -58,12 +58,14 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--pass-reps", type=int, default=20)
     p.add_argument("--workload", default="square2d",
-                   choices=("square2d", "lattice64", "cube3d", "sweep", "adjoint"),
+                   choices=("square2d", "lattice64", "cube3d", "sweep", "adjoint", "fig5", "passes"),
                    help="square2d (default): the headline 2-D square-array sweep; the others measure the "
                         "64^2 FP64 lattice, the 3-D cubic arrays, the batched complex-sigma_1 sweep and the "
                         "adjoint (gradient) configuration, one JSON line each")
     p.add_argument("--sweep-sigmas", type=int, default=16, help="sweep: sigma_1 values per microstructure per step")
     p.add_argument("--fd-voxels", type=int, default=16, help="adjoint: voxels checked by central differences")
+    p.add_argument("--fig-iters", type=int, default=600, help="fig5: iteration cap per curve")
+    p.add_argument("--dim", type=int, default=2, choices=(2, 3), help="passes: 2-D or 3-D square array")
     return p.parse_args()
 
 
@@ -229,6 +231,19 @@ def run_reference(args, sigmas):
     print(json.dumps(line), flush=True)
 
 
+def combine_ranks(elapsed: float, units: float, device="cpu"):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks.
+    Needs an initialised process group (nccl on the GPUs, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -298,11 +313,7 @@ def run_ours(args, sigmas):
     vox = sum(it * N for stp in results for (_, _, it, _, _, _, _) in stp)
     launches = sum(kl for stp in results for (*_, kl) in stp)
     if world > 1:
-        t = torch.tensor([elapsed, vox], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        elapsed, vox = float(tmax[0]), float(t[1])
+        elapsed, vox = combine_ranks(elapsed, vox, dev)
     value = vox / elapsed
 
     # per-solve summary of the last timed step: iterations and time to the stop rule
@@ -627,6 +638,97 @@ def run_adjoint(args):
           fd_median_rel_err=float(np.median(errs)))
 
 
+def run_passes(args):
+    """Pass timing alone (the unit the profiles capture): after one lsfft_prepare per
+    scheme, `--pass-reps` launches of the row pass, then of the strided pass(es), on
+    the square array at sigma_1 = 10, FP32, trig symbol; CUDA events on the grid's
+    stream.  `--dim 3` uses the n^3 cubic array (n <= 512)."""
+    torch, L = _gpu_setup()
+    d = args.dim
+    n = args.n if d == 2 else min(args.n, 512)
+    mask = square_array_mask(n, d=d)
+    N = mask.size
+    e = [1.0] + [0.0] * (d - 1)
+    stream = torch.cuda.Stream()
+    peak, _ = measured_peaks()
+    frac = 0.25 if d == 2 else 0.125
+    out = {}
+    with L.Grid(mask, stream=stream.cuda_stream) as g:
+        for sch in SCHEMES:
+            g.prepare(10.0, e, scheme=sch, precision="fp32", green=args.green, tol=0.0, max_iter=100000,
+                      alpha=ALPHA_BETA[0], beta=ALPHA_BETA[1])
+            packed = d == 2
+            for kind, name in ((0, "row"), (1, "col")):
+                with torch.cuda.stream(stream):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    g.launch_passes(kind, args.pass_reps)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / args.pass_reps
+                byt = algorithmic_bytes(name, sch, N, d=d, fraction=frac, packed=packed)
+                if name == "col" and d == 3:
+                    byt *= 3
+                out[f"{name}|{sch}"] = {"ms": round(ms, 4), "alg_bytes": int(byt), "GBps": round(byt / ms / 1e6, 1),
+                                        "frac_of_measured_hbm": round(byt / ms / 1e6 / peak, 4)}
+    _line("pass time (row pass / strided pass)", out["col|ms"]["ms"], "ms", args,
+          {"workload": f"square array {'x'.join([str(n)] * d)}, sigma1 = 10, FP32, {args.green} symbol, "
+                       f"{args.pass_reps} launches per pass kind after lsfft_prepare", "n": n, "d": d},
+          dtype="f32" if d == 2 else "c64", higher_is_better=False, passes=out)
+
+
+def run_fig5(args):
+    """The Moulinec-Suquet experiment of the section on their numerical example:
+    square array of squares at 25 %, sigma_1 = 0 (insulating squares), sigma_2 = 1,
+    pole interval estimate [1/4, 4]; convergence of sigma_k for MS against MS in
+    H'' (their first figure) and for EM against EM in H'' (their second).  The
+    curves are the relative distance of sigma_k to the converged discrete value and
+    to Obnosov's continuum value sqrt(1/3) (Eq. J47a), per iteration, FP64.
+
+    EM with the reference sqrt(sigma_1 sigma_2) is undefined at sigma_1 = 0; its
+    curve uses the per-voxel mode with the reference 1/2 (the MS reference)."""
+    torch, L = _gpu_setup()
+    n = args.n if args.n <= 4096 else 2048
+    mask = square_array_mask(n)
+    e = [1.0, 0.0]
+    obn = math.sqrt(1.0 / 3.0)
+    out = {}
+    t0 = time.perf_counter()
+    vox = 0
+    with L.Grid(mask) as g:
+        for green in ("fd", "trig"):
+            ref = g.solve(0.0, e, scheme="em_sub", precision="fp64", green=green, tol=1e-13, max_iter=4000,
+                          alpha=0.25, beta=4.0)
+            s_ref = ref.sigma_star.real
+            ref.free()
+            for sch in ("ms", "ms_sub", "em", "em_sub"):
+                kw = dict(scheme=sch, precision="fp64", green=green, tol=1e-11, max_iter=args.fig_iters,
+                          alpha=0.25, beta=4.0)
+                if sch == "em":
+                    g.set_sigma_field(1.0 - mask.astype(np.float64), sigma0=0.5)
+                    r = g.solve(1.0, e, **kw)
+                    g.set_sigma_field(None)
+                else:
+                    r = g.solve(0.0, e, **kw)
+                vox += r.iterations * mask.size
+                h = r.hist_sigma.real
+                err = np.abs(h - s_ref) / s_ref
+                first = {f"1e-{p}": (int(np.argmax(err < 10.0 ** -p)) if np.any(err < 10.0 ** -p) else None)
+                         for p in range(2, 11, 2)}
+                out[f"{green}|{sch}"] = {
+                    "iters": r.iterations, "status": r.status, "sigma_star": r.sigma_star.real,
+                    "rel_err_vs_obnosov": abs(r.sigma_star.real - obn) / obn, "discrete_limit": s_ref,
+                    "first_iter_below": first,
+                    "curve_rel_err_vs_limit": [float(f"{x:.3g}") for x in err[:200]]}
+                r.free()
+    dt = time.perf_counter() - t0
+    _line("iterations to a relative sigma_* error (sigma_1 = 0 experiment)", vox / dt, UNIT, args,
+          {"workload": f"{n}x{n} square array of squares (f = 1/4), sigma_1 = 0, sigma_2 = 1, e = (1, 0), "
+                       "[alpha, beta] = [1/4, 4], FP64, fd and trig Green symbols; EM with reference 1/2 "
+                       "through the per-voxel mode", "n": n, "obnosov_sigma_star": obn},
+          dtype="c128", curves=out)
+
+
 def main():
     args = parse()
     sigmas = tuple(float(s) for s in args.sigmas.split(","))
@@ -635,7 +737,8 @@ def main():
     elif args.workload == "square2d":
         run_ours(args, sigmas)
     else:
-        {"lattice64": run_lattice64, "cube3d": run_cube3d, "sweep": run_sweep, "adjoint": run_adjoint}[
+        {"lattice64": run_lattice64, "cube3d": run_cube3d, "sweep": run_sweep, "adjoint": run_adjoint,
+         "fig5": run_fig5, "passes": run_passes}[
             args.workload](args)
 
 

@@ -412,6 +412,27 @@ class Grid:
             a = np.ascontiguousarray(np.asarray(sigma), dtype=np.complex128)
             lsfft_set_sigma_field(self.handle, a.ctypes.data, False, sigma0)
 
+    def effective_tensor(self, sigma1, **kw):
+        """The full d x d effective tensor from d solves with applied fields e_a.
+
+        The problem is linear in e and <J> = sigma_* <E> holds for any mask (Eq. J13),
+        so with the columns <J>_a and <E>_a of the d solves sigma_* = [<J>] [<E>]^-1.
+        <E>_a = e_a at the fixed point; the Eyre-Milton type schemes reach it only in
+        the limit, and the product form is their matrix analogue of the scalar
+        estimate <J>.e / <E>.e.  A mask without square symmetry gives an
+        anisotropic, possibly non-diagonal tensor.  Returns (tensor, results)."""
+        Jm = np.zeros((self.d, self.d), dtype=np.complex128)
+        Em = np.zeros((self.d, self.d), dtype=np.complex128)
+        results = []
+        for a in range(self.d):
+            e = np.zeros(self.d)
+            e[a] = 1.0
+            r = self.solve(sigma1, e, **kw)
+            Jm[:, a] = r.mean_J
+            Em[:, a] = r.mean_E
+            results.append(r)
+        return Jm @ np.linalg.inv(Em), results
+
     def gradient(self, result, e, grad_ptr=None):
         """(d sigma_*/d sigma_1, energy estimate); d sigma_*/d sigma(x) into grad_ptr."""
         return lsfft_gradient(self.handle, result._ptr, e, grad_ptr)

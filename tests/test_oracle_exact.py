@@ -111,3 +111,20 @@ def test_lanczos_nodes_reproduce_measure_and_hull(green):
         a, b, _, _ = X.pole_hull(mm, w, 1e-10)
         la, lb = L.lanczos_hull(th, wt, 1e-10)
         assert abs(la - a) < 1e-6 * a and abs(lb - b) < 1e-6 * b
+
+
+def test_effective_tensor_diagonal_laminate_closed_form():
+    """Layers normal to n = (1,1)/sqrt 2 (mask a function of x + y), volume fraction
+    1/2, forward-difference symbol: the discrete fields are exactly one-dimensional,
+    so sigma_* = s_h n n^T + s_a (I - n n^T) with the harmonic and arithmetic means
+    (a non-diagonal tensor; the anisotropic case of Eq. J13)."""
+    n, w = 32, 4
+    s = (np.arange(n)[:, None] + np.arange(n)[None, :]) % (2 * w)
+    mask = (s < w).astype(np.uint8)
+    nn = np.full((2, 2), 0.5)
+    for s1 in (10.0, 0.2 + 0.7j):
+        sa = 0.5 * s1 + 0.5
+        sh = 1.0 / (0.5 / s1 + 0.5)
+        expect = sh * nn + sa * (np.eye(2) - nn)
+        got = X.effective_tensor(mask, s1, "fd")
+        np.testing.assert_allclose(got, expect, rtol=1e-11, atol=1e-12)

@@ -284,3 +284,28 @@ def test_substituted_em_rounding_stability_limit():
     k = int(np.argmax(ru.hist_field_norm > 1e3 * ru.hist_field_norm[0]))
     assert k > 0 and abs(ru.hist_sigma[k] - re_.sigma_star) < 1e-4 * abs(re_.sigma_star)
     assert rs.hist_field_norm.max() < 10 * rs.hist_field_norm[0]
+
+
+def test_insulating_squares_experiment():
+    """The sigma_1 = 0 experiment with [alpha, beta] = [1/4, 4]: MS (reference 1/2) and MS
+    in H'' share the bound 0.6 (Eq. J1 with the weighted eigenvalues in [1/5, 4/5];
+    Eq. J42a with t(0) = 1/4), EM in H'' has 1/3 (Eq. J46); all reach the same discrete
+    sigma_*, which lies within discretisation error of Eq. J47a."""
+    from oracle import constants as C
+
+    mask = square_array_mask(64)
+    e = np.array([1.0, 0.0])
+    assert abs(C.t_of_sigma1(0.0, 0.25, 4.0) - 0.25) < 1e-15
+    assert abs(S.predicted_rate("ms_sub", 0.0, 0.25, 4.0) - 0.6) < 1e-15
+    assert abs(S.predicted_rate("ms", 0.0, m_hull=(0.2, 0.8)) - 0.6) < 1e-15
+    assert abs(S.predicted_rate("em_sub", 0.0, 0.25, 4.0) - 1.0 / 3.0) < 1e-15
+    out = {}
+    for sch in ("ms", "ms_sub", "em_sub"):
+        r = S.solve(S.Problem(mask, 0.0, e, "fd"), sch, alpha=0.25, beta=4.0, tol=1e-10, max_iter=500)
+        assert r.status == S.STATUS_OK
+        out[sch] = r
+    s = out["ms"].sigma_star.real
+    for r in out.values():
+        assert abs(r.sigma_star - s) < 1e-9
+    assert out["em_sub"].iterations < out["ms"].iterations
+    assert abs(s - np.sqrt(1.0 / 3.0)) < 1e-3
