@@ -40,6 +40,7 @@ struct CluCfg {
     static constexpr int THREADS = cmin(512, LINES * TL);
     static constexpr int G = THREADS / TL;             // lines transformed concurrently
     static constexpr int ROUNDS = (LINES + G - 1) / G;
+    static constexpr bool SLOT_ROUNDS = G == W && ROUNDS == LS;   // round rd transforms exactly slot rd
     static constexpr int YP = M + 4;                   // staged line pitch (bank offset between lines)
     static constexpr int XP = roundup16(M + M / 16);   // exchange line pitch
     static constexpr int Y_BYTES = LINES * YP * CS;
@@ -150,10 +151,13 @@ col_pass_cluster(const PassArgs<T> A) {
         for (int s = 0; s < LS; ++s) prefetch_slot(item, s);
     for (; item < n_items; item += ncl) {
         const int64_t next = item + ncl;
-        cp_async_wait_all();
-        __syncthreads();
-        // 1. local forward M-point transforms, parked in place
+        // 1. local forward M-point transforms, parked in place.  When one round
+        //    covers exactly one slot (G == W), round rd starts as soon as slot rd
+        //    has landed, while the later slot is still in flight.
         for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
+            if (Cfg::SLOT_ROUNDS) cp_async_wait_pending(LS - 1 - rd);
+            else if (rd == 0) cp_async_wait_all();
+            __syncthreads();
             const int l = rd * G + g;
             C v[E];
             C* Yl = Y + (l < LINES ? l : 0) * YP;
@@ -220,7 +224,8 @@ col_pass_cluster(const PassArgs<T> A) {
         }
         cluster.sync();
         // 3. local inverse M-point transforms, parked in place; coalesced stores;
-        //    the next item's slots are staged as soon as they are stored
+        //    the next item's slots are staged as soon as they are stored (with
+        //    G == W, slot rd is stored and restaged while round rd + 1 computes)
         for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
             const int l = rd * G + g;
             C v[E];
@@ -232,12 +237,20 @@ col_pass_cluster(const PassArgs<T> A) {
 #pragma unroll
                 for (int m = 0; m < E; ++m) Yl[t + TL * m] = v[m];
             }
+            if (Cfg::SLOT_ROUNDS) {
+                __syncthreads();
+                store_slot(item, rd);
+                __syncthreads();
+                if (next < n_items) prefetch_slot(next, rd);
+            }
         }
-        __syncthreads();
-        for (int s = 0; s < LS; ++s) {
-            store_slot(item, s);
+        if (!Cfg::SLOT_ROUNDS) {
             __syncthreads();
-            if (next < n_items) prefetch_slot(next, s);
+            for (int s = 0; s < LS; ++s) {
+                store_slot(item, s);
+                __syncthreads();
+                if (next < n_items) prefetch_slot(next, s);
+            }
         }
     }
     cp_async_wait_all();

@@ -81,30 +81,90 @@ __device__ __forceinline__ C mul_root16(C a, int q) {
     return mkc(c * a.x - s * a.y, c * a.y + s * a.x);
 }
 
+// Paired FP32 arithmetic (sm_100 family): one instruction applies the same
+// operation to both halves of a 64-bit register pair, so a complex add or
+// subtract issues once instead of twice.  Its operands must sit in aligned
+// register pairs, which costs moves where registers are scarce: the kernels
+// enable it only where they run at most 256 threads per block.
+__device__ __forceinline__ unsigned long long pk2(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(d);
+}
+
+// Radix-2 butterfly with the odd leg rotated by exp(-+2 pi i q / 16):
+// (e + w o, e - w o).
+template <bool INV, bool PAIRED, typename C>
+__device__ __forceinline__ void butterfly16(const C& e, const C& o, int q, C& lo, C& hi) {
+    using T = decltype(e.x);
+    q &= 15;
+    if constexpr (PAIRED && sizeof(T) == 4) {
+        if (q == 0) {
+            lo = add2(e, o);
+            hi = sub2(e, o);
+            return;
+        }
+        if (q != 4 && q != 8 && q != 12) {
+            // w o = (c, c) o + (-s, s) (o.y, o.x) with w = c + i s
+            const float c = (float)cos16(q);
+            const float s = INV ? (float)sin16(q) : -(float)sin16(q);
+            const float2 t = fma2(mkc(-s, s), mkc(o.y, o.x), mul2(mkc(c, c), o));
+            lo = add2(e, t);
+            hi = sub2(e, t);
+            return;
+        }
+    }
+    const C t = mul_root16<INV>(o, q);
+    lo = cadd(e, t);
+    hi = csub(e, t);
+}
+
 // In-register DFT of the R elements a[OFF + STRIDE*i] (R | 16) into out[0..R-1],
 // natural order, by recursive even/odd splitting; every index is a template
 // constant so the whole transform stays in registers.
-template <int R, int STRIDE, int OFF, bool INV, typename C, int NA>
+template <int R, int STRIDE, int OFF, bool INV, bool PAIRED, typename C, int NA>
 __device__ __forceinline__ void dft_rec(const C (&a)[NA], C (&out)[R]) {
     if constexpr (R == 1) {
         out[0] = a[OFF];
     } else {
         C ev[R / 2], od[R / 2];
-        dft_rec<R / 2, 2 * STRIDE, OFF, INV>(a, ev);
-        dft_rec<R / 2, 2 * STRIDE, OFF + STRIDE, INV>(a, od);
+        dft_rec<R / 2, 2 * STRIDE, OFF, INV, PAIRED>(a, ev);
+        dft_rec<R / 2, 2 * STRIDE, OFF + STRIDE, INV, PAIRED>(a, od);
 #pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            const C t = mul_root16<INV>(od[k], k * (16 / R));
-            out[k] = cadd(ev[k], t);
-            out[k + R / 2] = csub(ev[k], t);
-        }
+        for (int k = 0; k < R / 2; ++k)
+            butterfly16<INV, PAIRED>(ev[k], od[k], k * (16 / R), out[k], out[k + R / 2]);
     }
 }
 
-template <int R, bool INV, typename C>
+template <int R, bool INV, bool PAIRED, typename C>
 __device__ __forceinline__ void dft(C (&a)[R]) {
     C out[R];
-    dft_rec<R, 1, 0, INV>(a, out);
+    dft_rec<R, 1, 0, INV, PAIRED>(a, out);
 #pragma unroll
     for (int i = 0; i < R; ++i) a[i] = out[i];
 }
@@ -113,7 +173,7 @@ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
 template <int N> struct LinePad { static constexpr int size = N + N / 16 + 1; };
 
-template <typename T, int N, int E, int RMAX, bool INV>
+template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false>
 struct LineFFT {
     using C = cx<T>;
     static constexpr int TL = N / E;   // threads per line
@@ -173,7 +233,7 @@ struct LineFFT {
 #pragma unroll
             for (int r = 0; r < R; ++r) a[r] = v[i + r * B];
             if constexpr (NS > 1) twiddle<R>(a, j % NS, NS * R, tw, tws);
-            dft<R, INV>(a);
+            dft<R, INV, PAIRED>(a);
             if constexpr (LAST) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[i + r * B] = a[r];

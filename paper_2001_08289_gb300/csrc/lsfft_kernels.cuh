@@ -72,7 +72,10 @@ struct RowCfg {
     static constexpr int M_BYTES = roundup16(LPB * N);
     static constexpr int SMEM = S_BYTES + X_BYTES + M_BYTES;
     static constexpr bool SUPPORTED = SMEM <= 227 * 1024 && THREADS <= 1024;
-    static constexpr int MINB = min_blocks(SMEM, THREADS);
+    // FP64 lines are bound by the FP64 pipe, not by latency: give them the
+    // registers of one block per SM rather than spill
+    static constexpr int MINB = sizeof(T) == 8 ? 1 : min_blocks(SMEM, THREADS);
+    static constexpr bool PAIRED = THREADS <= 256;
 };
 
 template <typename T, int N, int D>
@@ -94,6 +97,7 @@ struct ColCfg {
     static constexpr int SMEM = bytes(COLS);
     static constexpr bool SUPPORTED = SMEM <= 227 * 1024 && THREADS <= 1024;
     static constexpr int MINB = min_blocks(SMEM, THREADS);
+    static constexpr bool PAIRED = THREADS <= 256;
 };
 
 // ---------------------------------------------------------------------------
@@ -158,6 +162,12 @@ struct KConst {
     int scheme, green;
 };
 
+// Compile-time scheme selector for code specialised outside a loop.
+template <int V>
+struct SchemeTag {
+    static constexpr int value = V;
+};
+
 // ---------------------------------------------------------------------------
 // Pointwise scheme update on one voxel (all d components).
 //   q[c]   : Q component (real space) on entry; on exit the field handed to the
@@ -165,12 +175,12 @@ struct KConst {
 //   S, T   : read and written in place on phase-1 voxels (substituted schemes).
 //   E, J   : the physical fields of the current iterate, for the averages.
 // ---------------------------------------------------------------------------
-template <typename T, int D>
+template <typename T, int D, int SCH>
 __device__ __forceinline__ void pointwise(const KConst<T>& K, cx<T> (&q)[D], bool inc, cx<T>* __restrict__ Sv,
                                           cx<T>* __restrict__ Tv, int64_t cs, cx<T> (&E)[D], cx<T> (&J)[D],
                                           bool write_st) {
     using C = cx<T>;
-    if (K.scheme == SCHEME_MS) {            // Eq. J0-0: tau = (sigma/sigma_0 - 1) E
+    if constexpr (SCH == SCHEME_MS) {            // Eq. J0-0: tau = (sigma/sigma_0 - 1) E
         const C a = inc ? K.a_in : K.a_out;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -178,7 +188,7 @@ __device__ __forceinline__ void pointwise(const KConst<T>& K, cx<T> (&q)[D], boo
             J[c] = inc ? cmul(K.s1, q[c]) : q[c];
             q[c] = cmul(a, q[c]);
         }
-    } else if (K.scheme == SCHEME_EM) {     // W P with W = (sigma - sigma_0)/(sigma + sigma_0)
+    } else if constexpr (SCH == SCHEME_EM) {     // W P with W = (sigma - sigma_0)/(sigma + sigma_0)
         const C W = inc ? K.a_in : K.a_out;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -187,14 +197,14 @@ __device__ __forceinline__ void pointwise(const KConst<T>& K, cx<T> (&q)[D], boo
             J[c] = cscale(cadd(q[c], wp), (T)0.5);
             q[c] = wp;
         }
-    } else if (K.scheme == SCHEME_MATVEC) { // chi v (the operator chi Gamma_1 chi of the pole problem)
+    } else if constexpr (SCH == SCHEME_MATVEC) { // chi v (the operator chi Gamma_1 chi of the pole problem)
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             E[c] = inc ? q[c] : mkc((T)0, (T)0);
             J[c] = mkc((T)0, (T)0);
             q[c] = E[c];
         }
-    } else if (K.scheme == SCHEME_MS_SUB) { // Eq. J36, J42a: tau'' = (L''/sigma_0'' - 1) E''
+    } else if constexpr (SCH == SCHEME_MS_SUB) { // Eq. J36, J42a: tau'' = (L''/sigma_0'' - 1) E''
         if (inc) {
             C s[D];
 #pragma unroll
@@ -265,28 +275,28 @@ __device__ __forceinline__ void pointwise(const KConst<T>& K, cx<T> (&q)[D], boo
 // s = s_x + i s_y, tau = tau_x + i tau_y with S = i s, T = i tau.  Every
 // coefficient is real here; with p_2 = i q_2 and p_3 = i q_3 one has
 // p . (Q, S, T) = p_1 Q - q_2 s - q_3 tau componentwise.
-template <typename T>
-__device__ __forceinline__ void pointwise_packed(const KConst<T>& K, cx<T>& z, bool inc, cx<T>* __restrict__ Sv,
-                                                 cx<T>* __restrict__ Tv, cx<T>& E, cx<T>& J, bool write_st) {
+template <typename T, int SCH>
+__device__ __forceinline__ void pointwise_packed(const KConst<T>& K, cx<T>& z, bool inc, cx<T>& s, cx<T>& tt,
+                                                 cx<T>& E, cx<T>& J) {
+    // s, tt: S and T of a phase-1 voxel, updated in place (the caller loads and
+    // stores them); unused elsewhere.
     using C = cx<T>;
-    if (K.scheme == SCHEME_MS) {
+    if constexpr (SCH == SCHEME_MS) {
         E = z;
         J = inc ? cscale(z, K.s1.x) : z;
         z = cscale(z, inc ? K.a_in.x : K.a_out.x);
-    } else if (K.scheme == SCHEME_EM) {
+    } else if constexpr (SCH == SCHEME_EM) {
         const C wp = cscale(z, inc ? K.a_in.x : K.a_out.x);
         E = cscale(csub(z, wp), K.inv2s0.x);
         J = cscale(cadd(z, wp), (T)0.5);
         z = wp;
-    } else if (K.scheme == SCHEME_MS_SUB) {
+    } else if constexpr (SCH == SCHEME_MS_SUB) {
         if (inc) {
-            const C s = *Sv;
             const C cc = csub(cscale(z, K.p1.x), cscale(s, K.p2.y));
             E = z;
             J = cadd(z, cscale(cc, K.tm1p1.x));
-            const C sn = cneg(cadd(cscale(cc, K.k3.y), cscale(s, K.k2.x)));
+            s = cneg(cadd(cscale(cc, K.k3.y), cscale(s, K.k2.x)));
             z = cadd(cscale(cc, K.k1.x), cscale(z, K.k2.x));
-            if (write_st) *Sv = sn;
         } else {
             E = z;
             J = z;
@@ -294,19 +304,14 @@ __device__ __forceinline__ void pointwise_packed(const KConst<T>& K, cx<T>& z, b
         }
     } else {
         if (inc) {
-            const C s = *Sv, tt = *Tv;
             const C cc = csub(csub(cscale(z, K.p1.x), cscale(s, K.p2.y)), cscale(tt, K.p3.y));
             const C cc2 = cadd(cc, cc);
             const C wq = cscale(csub(z, cscale(cc2, K.p1.x)), K.w.x);
-            const C sn = cscale(csub(s, cscale(cc2, K.p2.y)), -K.w.x);
-            const C tn = cscale(csub(tt, cscale(cc2, K.p3.y)), K.w.x);
+            s = cscale(csub(s, cscale(cc2, K.p2.y)), -K.w.x);
+            tt = cscale(csub(tt, cscale(cc2, K.p3.y)), K.w.x);
             E = cscale(csub(z, wq), K.inv2s0.x);
             J = cscale(cadd(z, wq), (T)0.5);
             z = wq;
-            if (write_st) {
-                *Sv = sn;
-                *Tv = tn;
-            }
         } else {
             const C wq = cscale(z, K.w.x);
             E = cscale(csub(z, wq), K.inv2s0.x);
@@ -458,60 +463,105 @@ row_pass(const PassArgs<T> A) {
             C v[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
-            if (mode != MODE_ROW_FIRST) LineFFT<T, N, E, Cfg::RMAX, true>::run(v, Xb, t, A.tw);
+            if (mode != MODE_ROW_FIRST) LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
 #pragma unroll
             for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
         }
 
-        // 2. pointwise scheme update and volume averages on real-space values
+        // 2. pointwise scheme update and volume averages on real-space values,
+        //    specialised per scheme outside the loop over the thread's points
         if (active) {
             T sE[D][2], sJ[D][2], sE2 = 0;
 #pragma unroll
             for (int c = 0; c < D; ++c) sE[c][0] = sE[c][1] = sJ[c][0] = sJ[c][1] = 0;
             const bool wst = mode != MODE_ROW_OUTPUT;
-#pragma unroll 4
-            for (int m = 0; m < E; ++m) {
-                const int pos = t + TL * m;
-                const int64_t idx = base + pos;
-                const bool inc = Mb[g * N + pos] != 0;
+            const bool outm = mode == MODE_ROW_OUTPUT;
+            auto points = [&](auto tag) {
+                constexpr int SCH = decltype(tag)::value;
+                constexpr bool SUB = SCH == SCHEME_MS_SUB || SCH == SCHEME_EM_SUB;
                 if (A.packed) {
-                    C* zp = Sb + g * PS + pos;
-                    C z = *zp, Ez, Jz;
-                    if (A.sigma)
-                        pointwise_field_packed<T>(A.k, z, A.sigma[idx].x, Ez, Jz);
-                    else
-                        pointwise_packed<T>(A.k, z, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, Ez,
-                                            Jz, wst);
-                    *zp = z;
-                    sE[0][0] += Ez.x;
-                    sE[1][0] += Ez.y;
-                    sJ[0][0] += Jz.x;
-                    sJ[1][0] += Jz.y;
-                    sE2 += Ez.x * Ez.x + Ez.y * Ez.y;
-                    if (mode == MODE_ROW_OUTPUT) {
-                        A.Eout[idx] = mkc(Ez.x, (T)0);
-                        A.Eout[A.Ntot + idx] = mkc(Ez.y, (T)0);
+                    // in batches of HB points: phase flags, and S (T) of the phase-1
+                    // points, first, so that their global loads are in flight
+                    // together before the first use
+                    constexpr int HB = (sizeof(T) == 4 ? 8 : 1) < E ? (sizeof(T) == 4 ? 8 : 1) : E;
+                    constexpr int UNR = sizeof(T) == 4 ? E / HB : 4;   // FP64: registers are scarcer
+#pragma unroll UNR
+                    for (int m0 = 0; m0 < E; m0 += HB) {
+                        bool inc[HB];
+                        C sv[HB], tv[HB];
+#pragma unroll
+                        for (int h = 0; h < HB; ++h) {
+                            const int pos = t + TL * (m0 + h);
+                            inc[h] = Mb[g * N + pos] != 0;
+                            sv[h] = tv[h] = mkc((T)0, (T)0);
+                            if constexpr (SUB) {
+                                if (inc[h]) sv[h] = A.S[base + pos];
+                            }
+                            if constexpr (SCH == SCHEME_EM_SUB) {
+                                if (inc[h]) tv[h] = A.Tf[base + pos];
+                            }
+                        }
+#pragma unroll
+                        for (int h = 0; h < HB; ++h) {
+                            const int pos = t + TL * (m0 + h);
+                            const int64_t idx = base + pos;
+                            C* zp = Sb + g * PS + pos;
+                            C z = *zp, Ez, Jz;
+                            if (!SUB && A.sigma)
+                                pointwise_field_packed<T>(A.k, z, A.sigma[idx].x, Ez, Jz);
+                            else
+                                pointwise_packed<T, SCH>(A.k, z, inc[h], sv[h], tv[h], Ez, Jz);
+                            if constexpr (SUB) {
+                                if (inc[h] && wst) {
+                                    A.S[idx] = sv[h];
+                                    if constexpr (SCH == SCHEME_EM_SUB) A.Tf[idx] = tv[h];
+                                }
+                            }
+                            *zp = z;
+                            sE[0][0] += Ez.x;
+                            sE[1][0] += Ez.y;
+                            sJ[0][0] += Jz.x;
+                            sJ[1][0] += Jz.y;
+                            sE2 += Ez.x * Ez.x + Ez.y * Ez.y;
+                            if (outm) {
+                                A.Eout[idx] = mkc(Ez.x, (T)0);
+                                A.Eout[A.Ntot + idx] = mkc(Ez.y, (T)0);
+                            }
+                        }
                     }
                 } else {
-                    C q[D], Ev[D], Jv[D];
+#pragma unroll 4
+                    for (int m = 0; m < E; ++m) {
+                        const int pos = t + TL * m;
+                        const int64_t idx = base + pos;
+                        const bool inc = Mb[g * N + pos] != 0;
+                        C q[D], Ev[D], Jv[D];
 #pragma unroll
-                    for (int c = 0; c < D; ++c) q[c] = Sb[(c * LPB + g) * PS + pos];
-                    if (A.sigma)
-                        pointwise_field<T, D>(A.k, q, A.sigma[idx], Ev, Jv);
-                    else
-                        pointwise<T, D>(A.k, q, inc, A.S ? A.S + idx : nullptr, A.Tf ? A.Tf + idx : nullptr, A.Ntot,
-                                        Ev, Jv, wst);
+                        for (int c = 0; c < D; ++c) q[c] = Sb[(c * LPB + g) * PS + pos];
+                        if (!SUB && A.sigma)
+                            pointwise_field<T, D>(A.k, q, A.sigma[idx], Ev, Jv);
+                        else
+                            pointwise<T, D, SCH>(A.k, q, inc, A.S ? A.S + idx : nullptr,
+                                                 A.Tf ? A.Tf + idx : nullptr, A.Ntot, Ev, Jv, wst);
 #pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        Sb[(c * LPB + g) * PS + pos] = q[c];
-                        sE[c][0] += Ev[c].x;
-                        sE[c][1] += Ev[c].y;
-                        sJ[c][0] += Jv[c].x;
-                        sJ[c][1] += Jv[c].y;
-                        sE2 += Ev[c].x * Ev[c].x + Ev[c].y * Ev[c].y;
-                        if (mode == MODE_ROW_OUTPUT) A.Eout[c * A.Ntot + idx] = Ev[c];
+                        for (int c = 0; c < D; ++c) {
+                            Sb[(c * LPB + g) * PS + pos] = q[c];
+                            sE[c][0] += Ev[c].x;
+                            sE[c][1] += Ev[c].y;
+                            sJ[c][0] += Jv[c].x;
+                            sJ[c][1] += Jv[c].y;
+                            sE2 += Ev[c].x * Ev[c].x + Ev[c].y * Ev[c].y;
+                            if (outm) A.Eout[c * A.Ntot + idx] = Ev[c];
+                        }
                     }
                 }
+            };
+            switch (A.k.scheme) {
+                case SCHEME_MS: points(SchemeTag<SCHEME_MS>{}); break;
+                case SCHEME_EM: points(SchemeTag<SCHEME_EM>{}); break;
+                case SCHEME_MS_SUB: points(SchemeTag<SCHEME_MS_SUB>{}); break;
+                case SCHEME_EM_SUB: points(SchemeTag<SCHEME_EM_SUB>{}); break;
+                default: points(SchemeTag<SCHEME_MATVEC>{}); break;
             }
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -533,7 +583,7 @@ row_pass(const PassArgs<T> A) {
                 for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
                 __syncthreads();
                 if (has_next) prefetch_line(next, l);
-                LineFFT<T, N, E, Cfg::RMAX, false>::run(v, Xb, t, A.tw);
+                LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
                 if (active) {
 #pragma unroll
                     for (int m = 0; m < E; ++m) A.X[l * A.Ntot + base + t + TL * m] = v[m];
@@ -731,8 +781,8 @@ col_pass(const PassArgs<T> A) {
                 for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
                 __syncthreads();
                 if (has_next) prefetch_line(next, l);
-                if (mode == MODE_COL_INV) LineFFT<T, N, E, Cfg::RMAX, true>::run(v, Xb, t, A.tw);
-                else LineFFT<T, N, E, Cfg::RMAX, false>::run(v, Xb, t, A.tw);
+                if (mode == MODE_COL_INV) LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+                else LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
                 store_line(item, l, v);
             }
             continue;
@@ -745,7 +795,7 @@ col_pass(const PassArgs<T> A) {
             C* Sl = Sb + (l * COLS + g) * PS;
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
-            LineFFT<T, N, E, Cfg::RMAX, false>::run(v, Xb, t, A.tw);
+            LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
 #pragma unroll
             for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
         }
@@ -787,7 +837,7 @@ col_pass(const PassArgs<T> A) {
             for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
             __syncthreads();
             if (has_next) prefetch_line(next, l);
-            LineFFT<T, N, E, Cfg::RMAX, true>::run(v, Xb, t, A.tw);
+            LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
             store_line(item, l, v);
         }
     }
