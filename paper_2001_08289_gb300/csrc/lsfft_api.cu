@@ -454,6 +454,8 @@ KConst<T> make_kconst(const SchemeParams& P) {
     K.g_b = kc<T>(P.g_b, P.inv_ntot);
     K.g_a0 = kc<T>(P.g_a0, P.inv_ntot);
     K.g_ce = kc<T>(P.g_ce);
+    K.iq_in = kc<T>(P.iq_in);
+    K.iq_out = kc<T>(P.iq_out);
     for (int c = 0; c < 3; ++c) K.e[c] = (T)P.e[c];
     K.scheme = P.scheme;
     K.green = P.green;
@@ -492,6 +494,8 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
     A.partials = g->partials;
     for (int a = 0; a < 3; ++a) A.fd[a] = a < g->d ? (const cx<T>*)g->fd[a][p] : nullptr;
     A.Ntot = g->N;
+    A.hp = half_pitch(g->n[0]);
+    A.Nh = (g->N / g->n[0]) * A.hp;
     for (int a = 0; a < 3; ++a) A.n[a] = (int)g->n[a];
     return A;
 }
@@ -513,8 +517,7 @@ cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
     Geom geo;
     if (g->d == 2) col_dispatch<T, 2>(g->logn[axis], OP_QUERY, nullptr, nullptr, &geo);
     else col_dispatch<T, 3>(g->logn[axis], OP_QUERY, nullptr, nullptr, &geo);
-    const int64_t items = A->packed ? (g->n[0] / 2 + geo.per_block) / geo.per_block   // Hermitian column pairs
-                                    : (A->n_inner / geo.per_block) * A->n_outer;
+    const int64_t items = (A->n_inner + geo.per_block - 1) / geo.per_block * A->n_outer;
     if (geo.cluster > 0) {
         const int64_t ncl = items < geo.max_clusters ? items : (geo.max_clusters > 0 ? geo.max_clusters : 1);
         A->grid_blocks = (int)(ncl * geo.cluster);
@@ -532,6 +535,12 @@ cudaError_t launch_cols(lsfft_grid* g, int st) {
         A.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[1] : nullptr;
         A.ls = g->n[0];
         A.n_inner = g->n[0];
+        if (A.packed) {   // the two half-spectrum planes, columns k_x = 0..n_x/2
+            A.packed = 0;
+            A.Ntot = A.Nh;
+            A.ls = A.hp;
+            A.n_inner = g->n[0] / 2 + 1;
+        }
         A.outer_stride = 0;
         A.n_outer = 1;
         A.line_axis = 1;
@@ -643,6 +652,11 @@ int start_solve(lsfft_grid* g, int st) {
     if (rc0 != LSFFT_OK) return rc0;
     CK(cudaMemsetAsync(g->ctrl_dev, 0, sizeof(Ctrl), g->stream));
     CK(cudaEventRecord(g->ev0, g->stream));
+    if (g->packed) {   // padding columns of the half-spectrum planes: defined, never read back
+        const int64_t hp = half_pitch(g->n[0]), c0 = g->n[0] / 2 + 1;
+        CK(cudaMemset2DAsync((cx<T>*)g->X + c0, hp * sizeof(cx<T>), 0, (hp - c0) * sizeof(cx<T>),
+                             2 * (g->N / g->n[0]), g->stream));
+    }
     CK(launch_init<T>((cx<T>*)g->X, st >= 1 ? (cx<T>*)g->S : nullptr, st >= 2 ? (cx<T>*)g->T : nullptr, g->mask,
                       *g->prm_host, g->N, g->d, g->packed,
                       g->sigma64 ? (const cx<T>*)g->sigma_t : nullptr, g->sm_count, g->stream));

@@ -15,9 +15,9 @@
 // applies the Gamma step, runs the inverse combination and writes the results
 // back to the same remote slots it read.  Every slot is read and rewritten by
 // exactly one thread, so a second cluster barrier suffices before the local
-// inverse M-point transforms.  Lines of an item: packed layout, the two slots
-// of W Hermitian column pairs (partner column staged in reversed row order);
-// complex layout, the d = 2 component planes of W adjacent columns.
+// inverse M-point transforms.  Lines of an item: the d = 2 component planes
+// (complex layout) or the two half-spectrum planes (packed layout) of W
+// adjacent columns.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -32,7 +32,7 @@ struct CluCfg {
     static constexpr int M = N / CL;
     static constexpr int CS = (int)sizeof(cx<T>);
     static constexpr int W = 32 / CS;                  // adjacent columns per item
-    static constexpr int LS = 2;                       // slots per column (mirror pair or component)
+    static constexpr int LS = 2;                       // slots per column: the two planes
     static constexpr int LINES = LS * W;
     static constexpr int E = sizeof(T) == 4 ? 16 : 8;
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
@@ -66,45 +66,15 @@ col_pass_cluster(const PassArgs<T> A) {
     C* Y = reinterpret_cast<C*>(smem_raw);
     const int g = threadIdx.x / TL, t = threadIdx.x % TL;
     C* Xg = reinterpret_cast<C*>(smem_raw + Cfg::Y_BYTES) + g * XP;
-    const bool packed = A.packed != 0;
-    const int nx = A.n[0];
-    const int64_t n_items = packed ? (nx / 2 + W) / W : nx / W;
+    // lines of an item: the two component planes (slots) of W adjacent columns;
+    // n_inner need not be a multiple of W (the half-spectrum planes hold
+    // n_x/2 + 1 columns within a padded pitch): the last item runs into padding
+    const int64_t n_items = (A.n_inner + W - 1) / W;
 
     C* Yr[CL];                                          // the item buffers of every block of the cluster
 #pragma unroll
     for (int p = 0; p < CL; ++p) Yr[p] = cluster.map_shared_rank(Y, p);
 
-    // column, component plane and row order of line (s, w) of an item
-    struct LineRef {
-        int col;
-        int plane;
-        bool reversed;
-        bool load;
-        bool store;
-    };
-    auto line_ref = [&](int64_t item, int s, int w) {
-        LineRef r;
-        if (packed) {
-            const int64_t j = item * W + w;
-            const bool valid = j <= nx / 2;
-            const bool self = (j == 0) || (j == nx / 2);
-            r.col = valid ? (s == 0 ? (int)j : (int)((nx - j) % nx)) : 0;
-            r.plane = 0;
-            r.reversed = s == 1;
-            r.load = valid;
-            r.store = valid && !(s == 1 && self);
-        } else {
-            r.col = (int)(item * W + w);
-            r.plane = s;
-            r.reversed = false;
-            r.load = r.store = true;
-        }
-        return r;
-    };
-    auto phys_row = [&](const LineRef& r, int j) {   // logical row q + CL j
-        const int lr = q + CL * j;
-        return r.reversed ? (N - lr) % N : lr;
-    };
     // stage / store slot s (W lines) of an item: lanes run over the W adjacent
     // columns first.  THREADS is a multiple of W, so a thread keeps one column
     // w = threadIdx.x % W for the whole loop and only the row advances.
@@ -113,24 +83,19 @@ col_pass_cluster(const PassArgs<T> A) {
     const int j0 = threadIdx.x / W;
     constexpr int JSTEP = Cfg::THREADS / W;
     auto prefetch_slot = [&](int64_t item, int s) {
-        const LineRef r = line_ref(item, s, wt);
-        if (r.load) {
-            C* dst = Y + (s * W + wt) * YP;
-            const C* src = A.X + r.plane * A.Ntot + r.col;
-            for (int j = j0; j < M; j += JSTEP) {
-                const C* sp = src + (int64_t)phys_row(r, j) * A.ls;
-                if constexpr (sizeof(C) == 16) cp_async16(dst + j, sp);
-                else cp_async8(dst + j, sp);
-            }
+        C* dst = Y + (s * W + wt) * YP;
+        const C* src = A.X + s * A.Ntot + item * W + wt;
+        for (int j = j0; j < M; j += JSTEP) {
+            const C* sp = src + (int64_t)(q + CL * j) * A.ls;
+            if constexpr (sizeof(C) == 16) cp_async16(dst + j, sp);
+            else cp_async8(dst + j, sp);
         }
         cp_async_commit();
     };
     auto store_slot = [&](int64_t item, int s) {
-        const LineRef r = line_ref(item, s, wt);
-        if (!r.store) return;
         const C* src = Y + (s * W + wt) * YP;
-        C* dst = A.X + r.plane * A.Ntot + r.col;
-        for (int j = j0; j < M; j += JSTEP) dst[(int64_t)phys_row(r, j) * A.ls] = src[j];
+        C* dst = A.X + s * A.Ntot + item * W + wt;
+        for (int j = j0; j < M; j += JSTEP) dst[(int64_t)(q + CL * j) * A.ls] = src[j];
     };
     // W_N^(p k) for p = 0..CL-1 (forward sign)
     auto twiddles = [&](int k, C (&w)[CL]) {
@@ -190,22 +155,14 @@ col_pass_cluster(const PassArgs<T> A) {
                 x[s][1] = cadd(a1, b1r);
                 x[s][3] = csub(a1, b1r);
             }
-            const LineRef r0 = line_ref(item, 0, w);
+            const int kx = (int)(item * W + w);
 #pragma unroll
             for (int m = 0; m < CL; ++m) {
-                const int ky = k + M * m;
-                if (packed) {
-                    C z1 = x[0][m], z2 = x[1][m];
-                    gamma_packed<T>(z1, z2, r0.load ? r0.col : 0, ky, A);
-                    x[0][m] = z1;
-                    x[1][m] = z2;
-                } else {
-                    C vq[2] = {x[0][m], x[1][m]};
-                    const int ki[3] = {r0.col, ky, 0};
-                    gamma_apply<T, 2>(vq, ki, A);
-                    x[0][m] = vq[0];
-                    x[1][m] = vq[1];
-                }
+                C vq[2] = {x[0][m], x[1][m]};
+                const int ki[3] = {kx, k + M * m, 0};
+                gamma_apply<T, 2>(vq, ki, A);
+                x[0][m] = vq[0];
+                x[1][m] = vq[1];
             }
 #pragma unroll
             for (int s = 0; s < LS; ++s) {

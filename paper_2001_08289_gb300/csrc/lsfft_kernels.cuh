@@ -58,6 +58,11 @@ __host__ __device__ constexpr int min_blocks(int smem, int threads) {
     return cmax(1, cmin(cmin(4, (227 * 1024) / (smem + 1024)), 2048 / threads));
 }
 
+// Row pitch (elements) of the two half-spectrum planes of the packed layout:
+// k_x = 0..n_x/2 plus padding to a 32-byte multiple, so that the strided pass can
+// move whole 32-byte row segments of any aligned group of adjacent columns.
+__host__ __device__ constexpr int64_t half_pitch(int64_t nx) { return nx / 2 + 4; }
+
 template <typename T, int N, int D>
 struct RowCfg {
     static constexpr int CS = (int)sizeof(cx<T>);
@@ -158,6 +163,7 @@ struct KConst {
     cx<T> s0, inv_s0;           // per-voxel conductivity mode: reference medium and its inverse
     cx<T> g_a, g_b, g_a0;       // Gamma step coefficients, already divided by N
     cx<T> g_ce;                 // zero-mode source coefficient
+    cx<T> iq_in, iq_out;        // initial Q = iq e per phase (two-phase media)
     T e[3];
     int scheme, green;
 };
@@ -366,7 +372,7 @@ __device__ __forceinline__ void pointwise_field_packed(const KConst<T>& K, cx<T>
 
 template <typename T>
 struct PassArgs {
-    cx<T>* X;                 // state, [D][Ntot] (packed: plane 0 only)
+    cx<T>* X;                 // state, [D][Ntot]; packed: [2][Nh], rows of hp, k_x = 0..n_x/2
     cx<T>* S;                 // H'' S component, [D][Ntot] (or null)
     cx<T>* Tf;                // H'' T component, [D][Ntot] (or null)
     cx<T>* Eout;              // output field, [D][Ntot] (row pass, output mode)
@@ -376,7 +382,9 @@ struct PassArgs {
     double* partials;         // [gridDim.x][NV]
     const cx<T>* tw;          // FP64 twiddle table W_N^k of the pass's line length
     const cx<T>* fd[3];       // forward-difference symbol u_a(k), per axis
-    int64_t Ntot;
+    int64_t Ntot;             // voxels; plane stride of the strided passes
+    int64_t hp;               // packed layout: row pitch of the two half-spectrum planes
+    int64_t Nh;               // packed layout: plane stride of the half-spectrum planes
     int64_t n_lines;          // row pass: number of rows
     int64_t ls;               // strided pass: element stride along the line
     int64_t n_inner;          // strided pass: contiguous line starts per outer slab
@@ -386,7 +394,7 @@ struct PassArgs {
     int line_axis;            // strided pass: 1 (y) or 2 (z)
     int mode;                 // PassMode
     int grid_blocks;          // persistent grid size chosen by the host
-    int packed;               // packed real layout (2-D only)
+    int packed;               // packed real layout (2-D row pass only; the strided pass sees two planes)
     KConst<T> k;
 };
 
@@ -409,17 +417,25 @@ row_pass(const PassArgs<T> A) {
     C* Xb = reinterpret_cast<C*>(smem_raw + Cfg::S_BYTES) + g * PX;            // exchange line
     uint8_t* Mb = smem_raw + Cfg::S_BYTES + Cfg::X_BYTES;                      // [LPB][N]
     const int64_t n_items = (A.n_lines + LPB - 1) / LPB;
-    const int L = A.packed ? 1 : D;
+    // staged lines per row: the d component planes, or in the packed layout the
+    // two half-spectrum planes (none on the first pass, which starts from the mask)
+    const int L = A.packed ? 2 : D;
+    const bool stage_x = !(A.packed && mode == MODE_ROW_FIRST);
+    constexpr int HP = (int)half_pitch(N);
 
     // Stage line l of the rows of `item` (and the mask with line 0): one commit group.
     auto prefetch_line = [&](int64_t item, int l) {
         constexpr int CH = N * (int)sizeof(C) / 16;          // 16-byte chunks per line
-        for (int i = threadIdx.x; i < LPB * CH; i += Cfg::THREADS) {
-            const int ch = i % CH, r = i / CH;
+        constexpr int HCH = HP * (int)sizeof(C) / 16;        // ... per half-spectrum row
+        const int ch_line = A.packed ? HCH : CH;
+        const C* src0 = A.packed ? A.X + l * A.Nh : A.X + l * A.Ntot;
+        const int64_t pitch = A.packed ? HP : N;
+        for (int i = threadIdx.x; stage_x && i < LPB * ch_line; i += Cfg::THREADS) {
+            const int ch = i % ch_line, r = i / ch_line;
             const int64_t row = item * LPB + r;
             if (row < A.n_lines)
                 cp_async16(reinterpret_cast<unsigned char*>(Sb + (l * LPB + r) * PS) + 16 * ch,
-                           reinterpret_cast<const unsigned char*>(A.X + l * A.Ntot + row * N) + 16 * ch);
+                           reinterpret_cast<const unsigned char*>(src0 + row * pitch) + 16 * ch);
         }
         if (l == 0) {
             constexpr int MCH = N / 16;
@@ -456,16 +472,55 @@ row_pass(const PassArgs<T> A) {
         const bool has_next = next < n_items;
 
         // 1. inverse x-DFT of every line, parked at this thread's own positions
-        for (int l = 0; l < L; ++l) {
-            cp_async_wait_pending(L - 1 - l);
+        if (A.packed) {
+            // Z = E_x + i E_y from the half spectra: Z(k) = X(k) + i Y(k) for
+            // k <= n/2 and conj(X(n-k)) + i conj(Y(n-k)) above (X, Y are the
+            // spectra of real rows); the first pass starts from Q = iq e instead
+            cp_async_wait_all();
             __syncthreads();
-            C* Sl = Sb + (l * LPB + g) * PS;
             C v[E];
+            if (mode == MODE_ROW_FIRST) {
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
-            if (mode != MODE_ROW_FIRST) LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+                for (int m = 0; m < E; ++m) {
+                    const int pos = t + TL * m;
+                    T q;
+                    if (A.sigma)
+                        q = A.k.scheme == SCHEME_EM ? A.sigma[base + pos].x + A.k.s0.x : (T)1;
+                    else
+                        q = Mb[g * N + pos] ? A.k.iq_in.x : A.k.iq_out.x;
+                    v[m] = mkc(q * A.k.e[0], q * A.k.e[1]);
+                }
+            } else {
+                const C* Hx = Sb + g * PS;
+                const C* Hy = Sb + (LPB + g) * PS;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int k = t + TL * m;
+                    if (k <= N / 2) {
+                        const C x = Hx[k], y = Hy[k];
+                        v[m] = mkc(x.x - y.y, x.y + y.x);
+                    } else {
+                        const C x = Hx[N - k], y = Hy[N - k];
+                        v[m] = mkc(x.x + y.y, y.x - x.y);
+                    }
+                }
+                LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+            }
+            C* Sl = Sb + g * PS;
 #pragma unroll
             for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
+        } else {
+            for (int l = 0; l < L; ++l) {
+                cp_async_wait_pending(L - 1 - l);
+                __syncthreads();
+                C* Sl = Sb + (l * LPB + g) * PS;
+                C v[E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+                if (mode != MODE_ROW_FIRST) LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+#pragma unroll
+                for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
+            }
         }
 
         // 2. pointwise scheme update and volume averages on real-space values,
@@ -575,7 +630,35 @@ row_pass(const PassArgs<T> A) {
 
         // 3. forward x-DFT and store; the next item's line l is staged as soon as
         //    every thread has read line l of this item
-        if (mode != MODE_ROW_OUTPUT) {
+        if (mode != MODE_ROW_OUTPUT && A.packed) {
+            // forward DFT of Z, then the half spectra X = (Z(k) + conj Z(n-k))/2,
+            // Y = (Z(k) - conj Z(n-k))/(2i) for k = 0..n/2 (the partner values
+            // come through the exchange buffer)
+            C* Sl = Sb + g * PS;
+            C v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+            __syncthreads();
+            if (has_next)
+                for (int l = 0; l < L; ++l) prefetch_line(next, l);
+            LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < E; ++m) Xb[pad16(t + TL * m)] = v[m];
+            __syncthreads();
+            if (active) {
+                C* Ho = A.X + row * HP;
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int k = t + TL * m;
+                    if (k <= N / 2) {
+                        const C z = v[m], zp = Xb[pad16((N - k) & (N - 1))];
+                        Ho[k] = mkc((T)0.5 * (z.x + zp.x), (T)0.5 * (z.y - zp.y));
+                        Ho[A.Nh + k] = mkc((T)0.5 * (z.y + zp.y), (T)0.5 * (zp.x - z.x));
+                    }
+                }
+            }
+        } else if (mode != MODE_ROW_OUTPUT) {
             for (int l = 0; l < L; ++l) {
                 C* Sl = Sb + (l * LPB + g) * PS;
                 C v[E];
@@ -651,54 +734,12 @@ __device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], c
     for (int c = 0; c < D; ++c) v[c] = cadd(cmul(K.g_a, v[c]), cmul(proj, u[c]));
 }
 
-// Packed 2-D Gamma step on a Hermitian pair: z1 = Z(k), z2 = Z(-k) with
-// Z = F_x + i F_y the transform of two real fields.  F_x(k) = (z1 + conj z2)/2,
-// F_y(k) = (z1 - conj z2)/(2i); after the (real-coefficient) Gamma step the
-// outputs are repacked as Z'(k) = F'_x(k) + i F'_y(k) and
-// Z'(-k) = conj F'_x(k) + i conj F'_y(k).
-template <typename T>
-__device__ __forceinline__ void gamma_packed(cx<T>& z1, cx<T>& z2, int kx, int ky, const PassArgs<T>& A) {
-    using C = cx<T>;
-    const KConst<T>& K = A.k;
-    const C tx = mkc((z1.x + z2.x) * (T)0.5, (z1.y - z2.y) * (T)0.5);
-    const C ty = mkc((z1.y + z2.y) * (T)0.5, (z2.x - z1.x) * (T)0.5);
-    C ox, oy;
-    if (kx == 0 && ky == 0) {
-        ox = mkc(K.g_a0.x * tx.x + K.g_ce.x * K.e[0], K.g_a0.x * tx.y);
-        oy = mkc(K.g_a0.x * ty.x + K.g_ce.x * K.e[1], K.g_a0.x * ty.y);
-    } else {
-        C ux, uy;
-        bool nyq = false;
-        if (K.green == GREEN_TRIG) {
-            const int nx = A.n[0], ny = A.n[1];
-            nyq = (kx == nx / 2) || (ky == ny / 2);
-            ux = mkc((T)(kx < nx / 2 ? kx : kx - nx), (T)0);
-            uy = mkc((T)(ky < ny / 2 ? ky : ky - ny), (T)0);
-        } else {
-            ux = A.fd[0][kx];
-            uy = A.fd[1][ky];
-        }
-        ox = cscale(tx, K.g_a.x);
-        oy = cscale(ty, K.g_a.x);
-        if (!nyq) {
-            const T nrm = ux.x * ux.x + ux.y * ux.y + uy.x * uy.x + uy.y * uy.y;
-            const C dot = cadd(cmulc(tx, ux), cmulc(ty, uy));
-            const C proj = cscale(dot, K.g_b.x / nrm);
-            ox = cadd(ox, cmul(proj, ux));
-            oy = cadd(oy, cmul(proj, uy));
-        }
-    }
-    z1 = mkc(ox.x - oy.y, ox.y + oy.x);
-    z2 = mkc(ox.x + oy.y, oy.x - ox.y);
-}
-
 // ---------------------------------------------------------------------------
 // Strided pass: lines along y (or z) with element stride ls.  Work item =
-// COLS line starts (one per thread group): in the complex layout COLS adjacent
-// line starts of one outer slab with their d component lines; in the packed
-// 2-D layout COLS Hermitian column pairs (kx, nx - kx), the partner column
-// staged with reversed row order so that position k of its transform holds
-// Z(-kx, -k).  Columns 0 and nx/2 are their own partners.
+// COLS adjacent line starts of one outer slab (one per thread group) with their
+// d component lines.  In 2-D with the packed layout the components are the two
+// half-spectrum planes (k_x = 0..n_x/2), so Gamma(k_x, k_y) acts on each column
+// on its own.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int D>
 __global__ void __launch_bounds__(ColCfg<T, N, D>::THREADS, ColCfg<T, N, D>::MINB)
@@ -710,58 +751,35 @@ col_pass(const PassArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (A.ctrl->skipB) return;
     const int mode = A.mode;
-    const bool packed = A.packed != 0;
 
     C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][COLS][PS]
     const int g = threadIdx.x / TL, t = threadIdx.x % TL;
     C* Xb = reinterpret_cast<C*>(smem_raw + Cfg::S_BYTES) + g * PX;
-    const int L = packed ? 2 : D;
+    constexpr int L = D;
     const int nx = A.n[0];
-    const int64_t cblocks = packed ? (nx / 2 + COLS) / COLS : A.n_inner / COLS;
-    const int64_t n_items = cblocks * (packed ? 1 : A.n_outer);
+    // n_inner need not be a multiple of COLS (the half-spectrum planes hold
+    // n_x/2 + 1 columns within a padded pitch): the last group runs into padding
+    const int64_t cblocks = (A.n_inner + COLS - 1) / COLS;
+    const int64_t n_items = cblocks * A.n_outer;
 
-    // complex layout: first line start of an item
+    // first line start of an item
     auto item_base = [&](int64_t item) { return (item / cblocks) * A.outer_stride + (item % cblocks) * COLS; };
-    // packed layout: column of slot `l` of pair j (slot 1 is the partner)
-    auto pair_col = [&](int64_t j, int l) { return l == 0 ? (int)j : (int)((nx - j) % nx); };
 
     auto prefetch_line = [&](int64_t item, int l) {
-        const int64_t b0 = packed ? 0 : item_base(item);
+        const int64_t b0 = item_base(item);
         for (int i = threadIdx.x; i < COLS * N; i += Cfg::THREADS) {
             const int col = i % COLS, r = i / COLS;
             C* dst = Sb + (l * COLS + col) * PS + r;
-            const C* src;
-            if (packed) {
-                const int64_t j = item * COLS + col;
-                if (j > nx / 2) continue;
-                const int row = l == 0 ? r : (N - r) % N;
-                src = A.X + pair_col(j, l) + (int64_t)row * A.ls;
-            } else {
-                src = A.X + l * A.Ntot + b0 + col + (int64_t)r * A.ls;
-            }
+            const C* src = A.X + l * A.Ntot + b0 + col + (int64_t)r * A.ls;
             if constexpr (sizeof(C) == 16) cp_async16(dst, src);
             else cp_async8(dst, src);
         }
         cp_async_commit();
     };
     auto store_line = [&](int64_t item, int l, const C (&v)[E]) {
-        if (packed) {
-            const int64_t j = item * COLS + g;
-            if (j > nx / 2) return;
-            const bool self = (j == 0) || (j == nx / 2);
-            if (l == 1 && self) return;
-            C* dst = A.X + pair_col(j, l);
+        C* dst = A.X + l * A.Ntot + item_base(item) + g;
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int r = t + TL * m;
-                const int row = l == 0 ? r : (N - r) % N;
-                dst[(int64_t)row * A.ls] = v[m];
-            }
-        } else {
-            C* dst = A.X + l * A.Ntot + item_base(item) + g;
-#pragma unroll
-            for (int m = 0; m < E; ++m) dst[(int64_t)(t + TL * m) * A.ls] = v[m];
-        }
+        for (int m = 0; m < E; ++m) dst[(int64_t)(t + TL * m) * A.ls] = v[m];
     };
 
     int64_t item = blockIdx.x;
@@ -800,19 +818,7 @@ col_pass(const PassArgs<T> A) {
             for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
         }
         // 2. Gamma multiply at own positions
-        if (packed) {
-            const int kx = (int)(item * COLS + g);
-            C* S0 = Sb + g * PS;
-            C* S1 = Sb + (COLS + g) * PS;
-#pragma unroll 4
-            for (int m = 0; m < E; ++m) {
-                const int kl = t + TL * m;
-                C z1 = S0[kl], z2 = S1[kl];
-                gamma_packed<T>(z1, z2, kx <= nx / 2 ? kx : 0, kl, A);
-                S0[kl] = z1;
-                S1[kl] = z2;
-            }
-        } else {
+        {
             const int64_t inner = (item % cblocks) * COLS + g;
             const bool two_d = A.line_axis == 1;   // 2-D: inner = kx, line = ky; 3-D z: inner = kx + nx ky
             const int kx = two_d ? (int)inner : (int)(inner % nx);

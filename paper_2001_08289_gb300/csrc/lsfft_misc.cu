@@ -15,19 +15,15 @@ __global__ void init_state_kernel(cx<T>* __restrict__ X, cx<T>* __restrict__ S, 
                                   int packed, const cx<T>* __restrict__ sigma) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Ntot; i += (int64_t)gridDim.x * blockDim.x) {
         const bool inc = mask[i] != 0;
+        // (packed layout: the first row pass forms the initial Q itself)
         if (sigma) {   // per-voxel mode: MS starts from E = e, EM from P = (sigma + sigma_0) e
             const double qr = P.scheme == SCHEME_EM ? (double)sigma[i].x + P.s0[0] : 1.0;
             const double qi = P.scheme == SCHEME_EM ? (double)sigma[i].y + P.s0[1] : 0.0;
-            if (packed) {
-                X[i] = mkc((T)(qr * P.e[0]), (T)(qr * P.e[1]));
-            } else {
+            if (!packed)
                 for (int c = 0; c < d; ++c) X[c * Ntot + i] = mkc((T)(qr * P.e[c]), (T)(qi * P.e[c]));
-            }
             continue;
         }
         if (packed) {
-            const double q = inc ? P.iq_in[0] : P.iq_out[0];
-            X[i] = mkc((T)(q * P.e[0]), (T)(q * P.e[1]));
             if (S) S[i] = inc ? mkc((T)(P.is_in[1] * P.e[0]), (T)(P.is_in[1] * P.e[1])) : mkc((T)0, (T)0);
             if (Tf) Tf[i] = inc ? mkc((T)(P.it_in[1] * P.e[0]), (T)(P.it_in[1] * P.e[1])) : mkc((T)0, (T)0);
             continue;
