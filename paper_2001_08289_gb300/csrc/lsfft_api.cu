@@ -11,6 +11,7 @@
 #include <cmath>
 #include <complex>
 #include <map>
+#include <mutex>
 #include <vector>
 #include <string>
 #include <tuple>
@@ -512,6 +513,47 @@ cudaError_t launch_row(lsfft_grid* g, int st, int mode, cx<T>* Eout) {
     return row_dispatch<T, 3>(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link-time
+// dependence on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// TMA view of the two planes of a 2-D strided pass for the cluster kernel:
+// 8-byte elements; dimensions (x element within the row pitch, row residue
+// q < 4, inner row block j0 < 256, outer row block j1, plane), so that one box
+// {W columns, 1, 256, M/256, 1} is the rows q + 4 j of W adjacent columns.
+template <typename T>
+cudaError_t encode_cluster_map(PassArgs<T>* A, int ny, int W) {
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t cs = sizeof(cx<T>), epc = sizeof(cx<T>) / 8;
+    const int M = ny / 4;
+    if (M % 256 != 0) return cudaErrorInvalidValue;
+    const cuuint64_t row = (cuuint64_t)A->ls * cs;
+    cuuint64_t dims[5] = {(cuuint64_t)A->ls * epc, 4, 256, (cuuint64_t)(M / 256), 2};
+    cuuint64_t strides[4] = {row, 4 * row, 1024 * row, (cuuint64_t)A->Ntot * cs};
+    cuuint32_t box[5] = {(cuuint32_t)(W * epc), 1, 256, (cuuint32_t)(M / 256), 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(&A->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, (void*)A->X, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
     Geom geo;
@@ -519,6 +561,8 @@ cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
     else col_dispatch<T, 3>(g->logn[axis], OP_QUERY, nullptr, nullptr, &geo);
     const int64_t items = (A->n_inner + geo.per_block - 1) / geo.per_block * A->n_outer;
     if (geo.cluster > 0) {
+        cudaError_t e = encode_cluster_map<T>(A, (int)g->n[axis], geo.per_block);
+        if (e != cudaSuccess) return e;
         const int64_t ncl = items < geo.max_clusters ? items : (geo.max_clusters > 0 ? geo.max_clusters : 1);
         A->grid_blocks = (int)(ncl * geo.cluster);
     } else {
@@ -727,6 +771,10 @@ int poll_solve(lsfft_grid* g) {
     if (g->phase_finish) {
         g->phase_finish = false;
         const Ctrl& C = *g->ctrl_host;
+        if (C.fault) {
+            g_last_error = "a bounded wait for a TMA transfer gave up on the device; the solve is invalid";
+            return LSFFT_ECUDA;
+        }
         res->E_device = g->cur_E;
         g->cur_E = nullptr;
         res->iters = C.iter;

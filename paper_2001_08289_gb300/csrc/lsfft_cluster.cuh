@@ -1,4 +1,5 @@
-// Strided (y) pass for long 2-D columns on a thread-block cluster.
+// Strided (y) pass for long 2-D columns on a thread-block cluster, with its
+// tiles moved by the tensor memory accelerator (TMA).
 //
 // One SM cannot stage enough adjacent columns of length N >= 2048 to read
 // whole 32-byte sectors, so a cluster of CL = 4 blocks shares the work of an
@@ -7,17 +8,24 @@
 // splits as
 //     X[k + M m] = sum_q W_CL^(q m) W_N^(q k) Y_q[k],
 //     Y_q[k]     = sum_j x[q + CL j] W_M^(j k),            k < M, m < CL.
-// Block q loads its rows of all item lines (coalesced across the W columns),
-// computes the M-point transforms Y_q in shared memory, and after one cluster
-// barrier each block takes a quarter of the k range: it reads Y_q[k] of every
-// block through distributed shared memory, forms the CL-point combinations
-// (all frequencies k + M m of all lines of the item are then in one thread),
-// applies the Gamma step, runs the inverse combination and writes the results
-// back to the same remote slots it read.  Every slot is read and rewritten by
-// exactly one thread, so a second cluster barrier suffices before the local
-// inverse M-point transforms.  Lines of an item: the d = 2 component planes
-// (complex layout) or the two half-spectrum planes (packed layout) of W
-// adjacent columns.
+// Block q fetches its rows of each plane of the item with one TMA box (rows
+// q + CL j, W columns; shared-memory layout [j][w]), computes the M-point
+// transforms Y_q in place, and after one cluster barrier each block takes a
+// quarter of the k range: it reads Y_q[k] of every block through distributed
+// shared memory, forms the CL-point combinations (all frequencies k + M m of
+// all lines of the item are then in one thread), applies the Gamma step, runs
+// the inverse combination and writes the results back to the same remote slots
+// it read.  Every slot is read and rewritten by exactly one thread, so a second
+// cluster barrier suffices before the local inverse M-point transforms.  Each
+// plane goes back by one TMA store as soon as its inverse transforms are done,
+// and the next item's plane is fetched into the same buffer as soon as that
+// store has read it, so loads and stores run under the transforms.  Lines of an
+// item: the d = 2 component planes (complex layout) or the two half-spectrum
+// planes (packed layout) of W adjacent columns.
+//
+// Staging the same tiles with one 8-byte copy per thread and row segment was
+// limited by the number of requests an SM keeps in flight; a TMA box is one
+// request for the whole tile.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -36,108 +44,163 @@ struct CluCfg {
     static constexpr int LINES = LS * W;
     static constexpr int E = sizeof(T) == 4 ? 16 : 8;
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
-    static constexpr int TL = M >= E ? M / E : 1;      // (only N >= 2048 is ever launched)
+    static constexpr int TL = M >= E ? M / E : 1;      // threads per line (only N >= 2048 is launched)
     static constexpr int THREADS = cmin(512, LINES * TL);
     static constexpr int G = THREADS / TL;             // lines transformed concurrently
-    static constexpr int ROUNDS = (LINES + G - 1) / G;
-    static constexpr bool SLOT_ROUNDS = G == W && ROUNDS == LS;   // round rd transforms exactly slot rd
-    static constexpr int YP = M + 4;                   // staged line pitch (bank offset between lines)
-    static constexpr int XP = roundup16(M + M / 16);   // exchange line pitch
-    static constexpr int Y_BYTES = LINES * YP * CS;
-    static constexpr int SMEM = Y_BYTES + G * XP * CS;
-    static constexpr bool SUPPORTED = N >= 2048 && SMEM <= 227 * 1024 && G >= 1 && (LINES % G == 0 || G > LINES);
+    static constexpr int SPR = G / W;                  // slots per round
+    static constexpr int ROUNDS = LS / (SPR > 0 ? SPR : 1);
+    static constexpr int BJ = 256;                     // rows of the inner TMA box dimension
+    static constexpr int EPC = CS / 8;                 // 8-byte tensor elements per complex value
+    static constexpr int SLOT_BYTES = M * W * CS;      // one plane of an item: [j][w]
+    // exchange line pitch: a multiple of 8 but not of 16 elements, so that the
+    // lines w and w + 1 of a warp at equal positions fall into disjoint banks
+    static constexpr int XP = roundup16(M + M / 16) + 8;
+    static constexpr int Y_BYTES = LS * SLOT_BYTES;
+    static constexpr int SMEM = Y_BYTES + G * XP * CS + 64;   // + two mbarriers
+    static constexpr bool SUPPORTED = N >= 2048 && SMEM <= 227 * 1024 && SPR >= 1 && G == SPR * W &&
+                                      LS % SPR == 0 && M % BJ == 0 && THREADS == G * TL;
 };
+
+// --- TMA and mbarrier primitives --------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Wait for the phase of the given parity to complete.  Gives up after `limit`
+// clock cycles and returns false: the caller records a fault and carries on, so
+// that every barrier of the cluster is still reached.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+// 5-D tiled TMA load (coordinates: x element, row residue q, inner row block,
+// outer row block, plane) completing on an mbarrier; and the matching store.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                             uint32_t src) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(map),
+        "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(src)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most n (0 or 1) bulk groups may still be reading shared memory
+__device__ __forceinline__ void bulk_wait_read(int n) {
+    if (n <= 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr long long MBAR_WAIT_LIMIT = 4000000000LL;   // clock cycles (about two seconds)
 
 template <typename T, int N>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(CluCfg<T, N>::THREADS, 1)
-col_pass_cluster(const PassArgs<T> A) {
+col_pass_cluster(const __grid_constant__ PassArgs<T> A) {
     namespace cg = cooperative_groups;
     using Cfg = CluCfg<T, N>;
     using C = cx<T>;
-    constexpr int CL = Cfg::CL, M = Cfg::M, W = Cfg::W, LS = Cfg::LS, LINES = Cfg::LINES;
-    constexpr int E = Cfg::E, TL = Cfg::TL, G = Cfg::G, YP = Cfg::YP, XP = Cfg::XP;
+    constexpr int CL = Cfg::CL, M = Cfg::M, W = Cfg::W, LS = Cfg::LS;
+    constexpr int E = Cfg::E, TL = Cfg::TL, XP = Cfg::XP, SPR = Cfg::SPR, EPC = Cfg::EPC, BJ = Cfg::BJ;
     constexpr int KQ = M / CL;                         // k range owned by one block in the exchange
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (A.ctrl->skipB) return;                         // uniform over the grid: no barrier is reached
 
     cg::cluster_group cluster = cg::this_cluster();
     const int q = (int)cluster.block_rank();
     const int64_t cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-    C* Y = reinterpret_cast<C*>(smem_raw);
-    const int g = threadIdx.x / TL, t = threadIdx.x % TL;
-    C* Xg = reinterpret_cast<C*>(smem_raw + Cfg::Y_BYTES) + g * XP;
-    // lines of an item: the two component planes (slots) of W adjacent columns;
+    C* Y = reinterpret_cast<C*>(smem_raw);             // [LS][M][W]
+    // thread -> (slot within the round, line position t, column w), columns fastest
+    const int w = threadIdx.x % W;
+    const int t = (threadIdx.x / W) % TL;
+    const int sl = threadIdx.x / (W * TL);
+    C* Xg = reinterpret_cast<C*>(smem_raw + Cfg::Y_BYTES) + (sl * W + w) * XP;
+    const uint32_t bar0 = smem_u32(smem_raw + Cfg::Y_BYTES + Cfg::G * XP * Cfg::CS);   // bars at bar0, bar0 + 8
+    const CUtensorMap* map = &A.tmap;
     // n_inner need not be a multiple of W (the half-spectrum planes hold
     // n_x/2 + 1 columns within a padded pitch): the last item runs into padding
     const int64_t n_items = (A.n_inner + W - 1) / W;
+    const bool leader = threadIdx.x == 0;
 
     C* Yr[CL];                                          // the item buffers of every block of the cluster
 #pragma unroll
     for (int p = 0; p < CL; ++p) Yr[p] = cluster.map_shared_rank(Y, p);
 
-    // stage / store slot s (W lines) of an item: lanes run over the W adjacent
-    // columns first.  THREADS is a multiple of W, so a thread keeps one column
-    // w = threadIdx.x % W for the whole loop and only the row advances.
-    static_assert(Cfg::THREADS % W == 0, "thread count must be a multiple of W");
-    const int wt = threadIdx.x % W;
-    const int j0 = threadIdx.x / W;
-    constexpr int JSTEP = Cfg::THREADS / W;
-    auto prefetch_slot = [&](int64_t item, int s) {
-        C* dst = Y + (s * W + wt) * YP;
-        const C* src = A.X + s * A.Ntot + item * W + wt;
-        for (int j = j0; j < M; j += JSTEP) {
-            const C* sp = src + (int64_t)(q + CL * j) * A.ls;
-            if constexpr (sizeof(C) == 16) cp_async16(dst + j, sp);
-            else cp_async8(dst + j, sp);
-        }
-        cp_async_commit();
+    auto load_slot = [&](int64_t item, int s) {         // leader only
+        const uint32_t bar = bar0 + 8 * s;
+        mbar_expect_tx(bar, Cfg::SLOT_BYTES);
+        tma_load_5d(smem_u32(Y) + s * Cfg::SLOT_BYTES, map, (int)(item * W * EPC), q, 0, 0, s, bar);
     };
-    auto store_slot = [&](int64_t item, int s) {
-        const C* src = Y + (s * W + wt) * YP;
-        C* dst = A.X + s * A.Ntot + item * W + wt;
-        for (int j = j0; j < M; j += JSTEP) dst[(int64_t)(q + CL * j) * A.ls] = src[j];
+    auto store_slot = [&](int64_t item, int s) {        // leader only
+        tma_store_5d(map, (int)(item * W * EPC), q, 0, 0, s, smem_u32(Y) + s * Cfg::SLOT_BYTES);
+        bulk_commit();
     };
     // W_N^(p k) for p = 0..CL-1 (forward sign)
-    auto twiddles = [&](int k, C (&w)[CL]) {
-        w[0] = mkc((T)1, (T)0);
+    auto twiddles = [&](int k, C (&tw)[CL]) {
+        tw[0] = mkc((T)1, (T)0);
         if constexpr (sizeof(T) == 4) {
             float s, c;
             sincospif(2.0f * (float)k / (float)N, &s, &c);
-            w[1] = mkc(c, -s);
+            tw[1] = mkc(c, -s);
         } else {
-            w[1] = A.tw[k];
+            tw[1] = A.tw[k];
         }
-        w[2] = cmul(w[1], w[1]);
-        w[3] = cmul(w[2], w[1]);
+        tw[2] = cmul(tw[1], tw[1]);
+        tw[3] = cmul(tw[2], tw[1]);
     };
+    static_assert(M % BJ == 0, "rows of a block must fill whole TMA boxes");
 
+    if (leader) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     int64_t item = cid;
-    if (item < n_items)
-        for (int s = 0; s < LS; ++s) prefetch_slot(item, s);
-    for (; item < n_items; item += ncl) {
+    if (leader && item < n_items)
+        for (int s = 0; s < LS; ++s) load_slot(item, s);
+    bool fault = false;
+    for (uint32_t it = 0; item < n_items; item += ncl, ++it) {
         const int64_t next = item + ncl;
-        // 1. local forward M-point transforms, parked in place.  When one round
-        //    covers exactly one slot (G == W), round rd starts as soon as slot rd
-        //    has landed, while the later slot is still in flight.
+        // 1. local forward M-point transforms in place; round rd covers slots
+        //    rd*SPR .. rd*SPR + SPR - 1 and starts when they have landed
         for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
-            if (Cfg::SLOT_ROUNDS) cp_async_wait_pending(LS - 1 - rd);
-            else if (rd == 0) cp_async_wait_all();
-            __syncthreads();
-            const int l = rd * G + g;
+            const int s = rd * SPR + sl;
+            if (!mbar_wait(bar0 + 8 * s, it & 1u, MBAR_WAIT_LIMIT)) fault = true;
+            C* Ys = Y + s * M * W;
             C v[E];
-            C* Yl = Y + (l < LINES ? l : 0) * YP;
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Yl[t + TL * m];
+            for (int m = 0; m < E; ++m) v[m] = Ys[(t + TL * m) * W + w];
             LineFFT<T, M, E, Cfg::RMAX, false>::run(v, Xg, t, A.tw, CL);
-            if (l < LINES) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) Yl[t + TL * m] = v[m];
-            }
+            for (int m = 0; m < E; ++m) Ys[(t + TL * m) * W + w] = v[m];
         }
         cluster.sync();
         // 2. exchange: combine, Gamma, inverse combine over the owned k range
         for (int idx = threadIdx.x; idx < W * KQ; idx += Cfg::THREADS) {
-            const int k = q * KQ + idx % KQ, w = idx / KQ;
+            const int wc = idx % W, k = q * KQ + idx / W;
             C tw[CL];
             twiddles(k, tw);
             C x[LS][CL];
@@ -145,7 +208,7 @@ col_pass_cluster(const PassArgs<T> A) {
             for (int s = 0; s < LS; ++s) {
                 C y[CL];
 #pragma unroll
-                for (int p = 0; p < CL; ++p) y[p] = cmul(Yr[p][(s * W + w) * YP + k], tw[p]);
+                for (int p = 0; p < CL; ++p) y[p] = cmul(Yr[p][(s * M + k) * W + wc], tw[p]);
                 // 4-point DFT over p: x[m] = sum_p y[p] (-i)^(p m)
                 const C a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
                 const C b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
@@ -155,7 +218,7 @@ col_pass_cluster(const PassArgs<T> A) {
                 x[s][1] = cadd(a1, b1r);
                 x[s][3] = csub(a1, b1r);
             }
-            const int kx = (int)(item * W + w);
+            const int kx = (int)(item * W + wc);
 #pragma unroll
             for (int m = 0; m < CL; ++m) {
                 C vq[2] = {x[0][m], x[1][m]};
@@ -176,41 +239,39 @@ col_pass_cluster(const PassArgs<T> A) {
                 y[1] = cadd(a1, b1r);
                 y[3] = csub(a1, b1r);
 #pragma unroll
-                for (int p = 0; p < CL; ++p) Yr[p][(s * W + w) * YP + k] = cmulc(y[p], tw[p]);
+                for (int p = 0; p < CL; ++p) Yr[p][(s * M + k) * W + wc] = cmulc(y[p], tw[p]);
             }
         }
         cluster.sync();
-        // 3. local inverse M-point transforms, parked in place; coalesced stores;
-        //    the next item's slots are staged as soon as they are stored (with
-        //    G == W, slot rd is stored and restaged while round rd + 1 computes)
+        // 3. local inverse M-point transforms in place.  After each round its
+        //    slots go out by TMA store; the slots of the round before are
+        //    restaged for the next item once their store has read them.
         for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
-            const int l = rd * G + g;
+            const int s = rd * SPR + sl;
+            C* Ys = Y + s * M * W;
             C v[E];
-            C* Yl = Y + (l < LINES ? l : 0) * YP;
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Yl[t + TL * m];
+            for (int m = 0; m < E; ++m) v[m] = Ys[(t + TL * m) * W + w];
             LineFFT<T, M, E, Cfg::RMAX, true>::run(v, Xg, t, A.tw, CL);
-            if (l < LINES) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) Yl[t + TL * m] = v[m];
-            }
-            if (Cfg::SLOT_ROUNDS) {
-                __syncthreads();
-                store_slot(item, rd);
-                __syncthreads();
-                if (next < n_items) prefetch_slot(next, rd);
+            for (int m = 0; m < E; ++m) Ys[(t + TL * m) * W + w] = v[m];
+            fence_proxy_async_smem();   // the TMA store reads what the threads wrote
+            __syncthreads();
+            if (leader) {
+                for (int j = 0; j < SPR; ++j) store_slot(item, rd * SPR + j);
+                if (rd > 0 && next < n_items) {
+                    bulk_wait_read(1);   // the store of round rd - 1 has read its slots
+                    for (int j = 0; j < SPR; ++j) load_slot(next, (rd - 1) * SPR + j);
+                }
             }
         }
-        if (!Cfg::SLOT_ROUNDS) {
-            __syncthreads();
-            for (int s = 0; s < LS; ++s) {
-                store_slot(item, s);
-                __syncthreads();
-                if (next < n_items) prefetch_slot(next, s);
-            }
+        if (leader && next < n_items) {
+            bulk_wait_read(0);
+            for (int j = 0; j < SPR; ++j) load_slot(next, (Cfg::ROUNDS - 1) * SPR + j);
         }
     }
-    cp_async_wait_all();
+    if (leader) bulk_wait_all();
+    if (fault) atomicExch(&A.ctrl->fault, 1);
     cluster.sync();   // no block leaves while a peer may still address its shared memory
 }
 

@@ -29,6 +29,8 @@
 // is issued, so loads overlap the remaining transforms of the current item.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the encoding itself goes through the runtime's driver entry point)
+
 #include "lsfft_fft.cuh"
 #include "lsfft_params.h"
 
@@ -396,6 +398,7 @@ struct PassArgs {
     int grid_blocks;          // persistent grid size chosen by the host
     int packed;               // packed real layout (2-D row pass only; the strided pass sees two planes)
     KConst<T> k;
+    CUtensorMap tmap;         // cluster strided pass: TMA view of the two planes (encoded by the host)
 };
 
 // ---------------------------------------------------------------------------

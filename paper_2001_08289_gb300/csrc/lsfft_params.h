@@ -44,7 +44,8 @@ struct Ctrl {
     int iter;        // number of sigma_k evaluated so far
     int run;         // consecutive relative changes below tol
     int status;      // ST_*
-    int pad0, pad1, pad2;
+    int fault;       // a bounded device wait gave up (the results are not valid)
+    int pad1, pad2;
     double prev[2];  // sigma_{k-1}
     double prev_norm;   // <|E_{k-1}|^2>
     double norm0;    // <|E_0|^2>
