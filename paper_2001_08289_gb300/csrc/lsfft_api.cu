@@ -534,18 +534,18 @@ EncodeTiledFn encode_tiled_fn() {
 
 // TMA view of the two planes of a 2-D strided pass for the cluster kernel:
 // 8-byte elements; dimensions (x element within the row pitch, row residue
-// q < 4, inner row block j0 < 256, outer row block j1, plane), so that one box
-// {W columns, 1, 256, M/256, 1} is the rows q + 4 j of W adjacent columns.
+// q < CL, inner row block j0 < 256, outer row block j1, plane), so that one box
+// {W columns, 1, 256, M/256, 1} is the rows q + CL j of W adjacent columns.
 template <typename T>
-cudaError_t encode_cluster_map(PassArgs<T>* A, int ny, int W) {
+cudaError_t encode_cluster_map(PassArgs<T>* A, int ny, int W, int CL) {
     EncodeTiledFn fn = encode_tiled_fn();
     if (!fn) return cudaErrorNotSupported;
     const cuuint64_t cs = sizeof(cx<T>), epc = sizeof(cx<T>) / 8;
-    const int M = ny / 4;
+    const int M = ny / CL;
     if (M % 256 != 0) return cudaErrorInvalidValue;
     const cuuint64_t row = (cuuint64_t)A->ls * cs;
-    cuuint64_t dims[5] = {(cuuint64_t)A->ls * epc, 4, 256, (cuuint64_t)(M / 256), 2};
-    cuuint64_t strides[4] = {row, 4 * row, 1024 * row, (cuuint64_t)A->Ntot * cs};
+    cuuint64_t dims[5] = {(cuuint64_t)A->ls * epc, (cuuint64_t)CL, 256, (cuuint64_t)(M / 256), 2};
+    cuuint64_t strides[4] = {row, CL * row, 256 * CL * row, (cuuint64_t)A->Ntot * cs};
     cuuint32_t box[5] = {(cuuint32_t)(W * epc), 1, 256, (cuuint32_t)(M / 256), 1};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     const CUresult r = fn(&A->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, (void*)A->X, dims, strides, box, estr,
@@ -561,7 +561,7 @@ cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
     else col_dispatch<T, 3>(g->logn[axis], OP_QUERY, nullptr, nullptr, &geo);
     const int64_t items = (A->n_inner + geo.per_block - 1) / geo.per_block * A->n_outer;
     if (geo.cluster > 0) {
-        cudaError_t e = encode_cluster_map<T>(A, (int)g->n[axis], geo.per_block);
+        cudaError_t e = encode_cluster_map<T>(A, (int)g->n[axis], geo.per_block, geo.cluster);
         if (e != cudaSuccess) return e;
         const int64_t ncl = items < geo.max_clusters ? items : (geo.max_clusters > 0 ? geo.max_clusters : 1);
         A->grid_blocks = (int)(ncl * geo.cluster);
