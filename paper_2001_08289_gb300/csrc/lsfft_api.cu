@@ -554,6 +554,30 @@ cudaError_t encode_cluster_map(PassArgs<T>* A, int ny, int W, int CL) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// TMA view of an item of the plain strided pass: 8-byte elements; dimensions
+// (x element of the line starts of a slab, inner line position j0 < 256, outer
+// line position j1, slab, plane), so that one box {COLS values, BJ0, BJ1, 1, d}
+// is every line of one item.
+template <typename T>
+cudaError_t encode_col_map(PassArgs<T>* A, int N, int cols, int d) {
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t cs = sizeof(cx<T>), epc = sizeof(cx<T>) / 8;
+    const int bj0 = N < 256 ? N : 256, bj1 = N / bj0;
+    const int64_t groups = (A->n_inner + cols - 1) / cols;
+    const cuuint64_t line = (cuuint64_t)A->ls * cs;
+    const cuuint64_t slab = A->n_outer > 1 ? (cuuint64_t)A->outer_stride * cs : (cuuint64_t)bj1 * bj0 * line;
+    cuuint64_t dims[5] = {(cuuint64_t)(groups * cols) * epc, (cuuint64_t)bj0, (cuuint64_t)bj1,
+                          (cuuint64_t)A->n_outer, (cuuint64_t)d};
+    cuuint64_t strides[4] = {line, bj0 * line, slab, (cuuint64_t)A->Ntot * cs};
+    cuuint32_t box[5] = {(cuuint32_t)(cols * epc), (cuuint32_t)bj0, (cuuint32_t)bj1, 1, (cuuint32_t)d};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(&A->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, (void*)A->X, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
     Geom geo;
@@ -567,6 +591,8 @@ cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
         A->grid_blocks = (int)(ncl * geo.cluster);
     } else {
         A->grid_blocks = (int)persistent_blocks(g, items, geo.blocks_per_sm);
+        cudaError_t e = encode_col_map<T>(A, (int)g->n[axis], geo.per_block, g->d);
+        if (e != cudaSuccess) return e;
     }
     if (g->d == 2) return col_dispatch<T, 2>(g->logn[axis], OP_LAUNCH, A, g->stream, nullptr);
     return col_dispatch<T, 3>(g->logn[axis], OP_LAUNCH, A, g->stream, nullptr);

@@ -33,6 +33,7 @@
 
 #include "lsfft_fft.cuh"
 #include "lsfft_params.h"
+#include "lsfft_tma.cuh"
 
 namespace lsfft {
 
@@ -57,7 +58,7 @@ struct Pitch {
 // passed to __launch_bounds__ so that registers do not become the tighter limit.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int min_blocks(int smem, int threads) {
-    return cmax(1, cmin(cmin(4, (227 * 1024) / (smem + 1024)), 2048 / threads));
+    return cmax(1, cmin(cmin(8, (227 * 1024) / (smem + 1024)), 2048 / threads));
 }
 
 // Row pitch (elements) of the two half-spectrum planes of the packed layout:
@@ -91,18 +92,20 @@ struct ColCfg {
     static constexpr int E = sizeof(T) == 4 ? (N < 16 ? N : 16) : (N < 8 ? N : 8);
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
     static constexpr int TL = N / E;
-    static constexpr int L = D > 2 ? D : 2;                       // staged lines per group
-    using P = Pitch<T, N, TL>;
-    static constexpr int bytes(int cols) { return cols * (L * P::S + P::X) * CS; }
-    static constexpr int CMAX = sizeof(T) == 4 ? 4 : 2;           // 32-byte sectors per row
-    static constexpr int fit(int cols) {
-        return cols == 0 ? 0 : ((bytes(cols) <= 110 * 1024 && cols * TL <= 512) ? cols : fit(cols / 2));
-    }
-    static constexpr int COLS = cmax(1, fit(CMAX));
-    static constexpr int THREADS = COLS * TL;
-    static constexpr int S_BYTES = COLS * L * P::S * CS;
+    static constexpr int EPC = CS / 8;                            // 8-byte tensor elements per value
+    static constexpr int item_bytes(int cols) { return D * N * cols * CS; }
+    static constexpr int xp() { return roundup16(N + N / 16) + 8; }
+    static constexpr int bytes(int cols) { return 2 * item_bytes(cols) + D * cols * xp() * CS + 64; }
+    // adjacent line starts per item: a 32-byte row segment, or 16 bytes when
+    // two item buffers of 32-byte segments do not fit
+    static constexpr int COLS = bytes(32 / CS) <= 220 * 1024 ? 32 / CS : 16 / CS;
+    static constexpr int THREADS = D * COLS * TL;                 // every line of an item at once
+    static constexpr int ITEM_BYTES = item_bytes(COLS);
+    static constexpr int XP = xp();
+    static constexpr int BJ0 = N < 256 ? N : 256;                 // TMA box rows: inner and outer dimension
+    static constexpr int BJ1 = N / BJ0;
     static constexpr int SMEM = bytes(COLS);
-    static constexpr bool SUPPORTED = SMEM <= 227 * 1024 && THREADS <= 1024;
+    static constexpr bool SUPPORTED = SMEM <= 227 * 1024 && THREADS <= 1024 && COLS * CS >= 16;
     static constexpr int MINB = min_blocks(SMEM, THREADS);
     static constexpr bool PAIRED = THREADS <= 256;
 };
@@ -170,9 +173,9 @@ struct KConst {
     int scheme, green;
 };
 
-// Compile-time scheme selector for code specialised outside a loop.
+// Compile-time integer (a scheme, a count) for code specialised outside a loop.
 template <int V>
-struct SchemeTag {
+struct IntTag {
     static constexpr int value = V;
 };
 
@@ -427,18 +430,22 @@ row_pass(const PassArgs<T> A) {
     constexpr int HP = (int)half_pitch(N);
 
     // Stage line l of the rows of `item` (and the mask with line 0): one commit group.
-    auto prefetch_line = [&](int64_t item, int l) {
-        constexpr int CH = N * (int)sizeof(C) / 16;          // 16-byte chunks per line
-        constexpr int HCH = HP * (int)sizeof(C) / 16;        // ... per half-spectrum row
-        const int ch_line = A.packed ? HCH : CH;
-        const C* src0 = A.packed ? A.X + l * A.Nh : A.X + l * A.Ntot;
-        const int64_t pitch = A.packed ? HP : N;
-        for (int i = threadIdx.x; stage_x && i < LPB * ch_line; i += Cfg::THREADS) {
-            const int ch = i % ch_line, r = i / ch_line;
+    // (chunk counts are compile-time constants in both branches: no runtime division)
+    auto stage_rows = [&](int64_t item, int l, const C* src0, auto chunks, int64_t pitch) {
+        constexpr int CHL = decltype(chunks)::value;
+        for (int i = threadIdx.x; i < LPB * CHL; i += Cfg::THREADS) {
+            const int ch = i % CHL, r = i / CHL;
             const int64_t row = item * LPB + r;
             if (row < A.n_lines)
                 cp_async16(reinterpret_cast<unsigned char*>(Sb + (l * LPB + r) * PS) + 16 * ch,
                            reinterpret_cast<const unsigned char*>(src0 + row * pitch) + 16 * ch);
+        }
+    };
+    auto prefetch_line = [&](int64_t item, int l) {
+        if (A.packed) {
+            if (stage_x) stage_rows(item, l, A.X + l * A.Nh, IntTag<HP * (int)sizeof(C) / 16>{}, HP);
+        } else {
+            stage_rows(item, l, A.X + l * A.Ntot, IntTag<N * (int)sizeof(C) / 16>{}, N);
         }
         if (l == 0) {
             constexpr int MCH = N / 16;
@@ -615,11 +622,11 @@ row_pass(const PassArgs<T> A) {
                 }
             };
             switch (A.k.scheme) {
-                case SCHEME_MS: points(SchemeTag<SCHEME_MS>{}); break;
-                case SCHEME_EM: points(SchemeTag<SCHEME_EM>{}); break;
-                case SCHEME_MS_SUB: points(SchemeTag<SCHEME_MS_SUB>{}); break;
-                case SCHEME_EM_SUB: points(SchemeTag<SCHEME_EM_SUB>{}); break;
-                default: points(SchemeTag<SCHEME_MATVEC>{}); break;
+                case SCHEME_MS: points(IntTag<SCHEME_MS>{}); break;
+                case SCHEME_EM: points(IntTag<SCHEME_EM>{}); break;
+                case SCHEME_MS_SUB: points(IntTag<SCHEME_MS_SUB>{}); break;
+                case SCHEME_EM_SUB: points(IntTag<SCHEME_EM_SUB>{}); break;
+                default: points(IntTag<SCHEME_MATVEC>{}); break;
             }
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -739,118 +746,105 @@ __device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], c
 
 // ---------------------------------------------------------------------------
 // Strided pass: lines along y (or z) with element stride ls.  Work item =
-// COLS adjacent line starts of one outer slab (one per thread group) with their
-// d component lines.  In 2-D with the packed layout the components are the two
-// half-spectrum planes (k_x = 0..n_x/2), so Gamma(k_x, k_y) acts on each column
-// on its own.
+// COLS adjacent line starts of one outer slab with their d component lines.  In
+// 2-D with the packed layout the components are the two half-spectrum planes
+// (k_x = 0..n_x/2), so Gamma(k_x, k_y) acts on each column on its own.
+//
+// One TMA box brings a whole item (all d planes, N rows of COLS adjacent
+// values: shared-memory layout [plane][row][column]) into one of two buffers,
+// two items ahead; every thread transforms one line position range of one
+// (plane, column) line, columns fastest, and stores its results from registers.
+// The buffer an item came in is refilled as soon as its last transform has read
+// it.  Staging the same tiles with 8-byte copies per thread was limited by the
+// number of requests an SM keeps in flight.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int D>
 __global__ void __launch_bounds__(ColCfg<T, N, D>::THREADS, ColCfg<T, N, D>::MINB)
-col_pass(const PassArgs<T> A) {
+col_pass(const __grid_constant__ PassArgs<T> A) {
     using Cfg = ColCfg<T, N, D>;
     using C = cx<T>;
-    constexpr int E = Cfg::E, TL = Cfg::TL, COLS = Cfg::COLS;
-    constexpr int PS = Cfg::P::S, PX = Cfg::P::X;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int E = Cfg::E, TL = Cfg::TL, COLS = Cfg::COLS, XP = Cfg::XP, EPC = Cfg::EPC;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (A.ctrl->skipB) return;
     const int mode = A.mode;
 
-    C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][COLS][PS]
-    const int g = threadIdx.x / TL, t = threadIdx.x % TL;
-    C* Xb = reinterpret_cast<C*>(smem_raw + Cfg::S_BYTES) + g * PX;
-    constexpr int L = D;
+    C* Bf = reinterpret_cast<C*>(smem_raw);                                    // [2][D][N][COLS]
+    const int w = threadIdx.x % COLS;
+    const int t = (threadIdx.x / COLS) % TL;
+    const int c = threadIdx.x / (COLS * TL);                                   // component plane
+    C* Xb = reinterpret_cast<C*>(smem_raw + 2 * Cfg::ITEM_BYTES) + (c * COLS + w) * XP;
+    const uint32_t bar0 = smem_u32(smem_raw + 2 * Cfg::ITEM_BYTES + D * COLS * XP * Cfg::CS);
     const int nx = A.n[0];
     // n_inner need not be a multiple of COLS (the half-spectrum planes hold
     // n_x/2 + 1 columns within a padded pitch): the last group runs into padding
     const int64_t cblocks = (A.n_inner + COLS - 1) / COLS;
     const int64_t n_items = cblocks * A.n_outer;
+    const bool leader = threadIdx.x == 0;
 
-    // first line start of an item
-    auto item_base = [&](int64_t item) { return (item / cblocks) * A.outer_stride + (item % cblocks) * COLS; };
-
-    auto prefetch_line = [&](int64_t item, int l) {
-        const int64_t b0 = item_base(item);
-        for (int i = threadIdx.x; i < COLS * N; i += Cfg::THREADS) {
-            const int col = i % COLS, r = i / COLS;
-            C* dst = Sb + (l * COLS + col) * PS + r;
-            const C* src = A.X + l * A.Ntot + b0 + col + (int64_t)r * A.ls;
-            if constexpr (sizeof(C) == 16) cp_async16(dst, src);
-            else cp_async8(dst, src);
-        }
-        cp_async_commit();
-    };
-    auto store_line = [&](int64_t item, int l, const C (&v)[E]) {
-        C* dst = A.X + l * A.Ntot + item_base(item) + g;
-#pragma unroll
-        for (int m = 0; m < E; ++m) dst[(int64_t)(t + TL * m) * A.ls] = v[m];
+    auto load_item = [&](int64_t item, int b) {   // leader only
+        const uint32_t bar = bar0 + 8 * b;
+        mbar_expect_tx(bar, Cfg::ITEM_BYTES);
+        tma_load_5d(smem_u32(Bf) + b * Cfg::ITEM_BYTES, &A.tmap, (int)((item % cblocks) * COLS * EPC), 0, 0,
+                    (int)(item / cblocks), 0, bar);
     };
 
+    if (leader) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
     int64_t item = blockIdx.x;
-    if (item < n_items)
-        for (int l = 0; l < L; ++l) prefetch_line(item, l);
-    for (; item < n_items; item += A.grid_blocks) {
-        const int64_t next = item + A.grid_blocks;
-        const bool has_next = next < n_items;
-        if (mode != MODE_COL_GAMMA) {
-            // forward-only or inverse-only transforms (3-D y passes)
-            for (int l = 0; l < L; ++l) {
-                cp_async_wait_pending(L - 1 - l);
-                __syncthreads();
-                C v[E];
-                C* Sl = Sb + (l * COLS + g) * PS;
+    if (leader) {
+        if (item < n_items) load_item(item, 0);
+        if (item + A.grid_blocks < n_items) load_item(item + A.grid_blocks, 1);
+    }
+    bool fault = false;
+    for (uint32_t it = 0; item < n_items; item += A.grid_blocks, ++it) {
+        const int b = it & 1;
+        const int64_t after = item + 2 * (int64_t)A.grid_blocks;   // the next item for this buffer
+        if (!mbar_wait(bar0 + 8 * b, (it >> 1) & 1u, MBAR_WAIT_LIMIT)) fault = true;
+        C* Bi = Bf + (size_t)b * D * N * COLS;
+        C* Yc = Bi + c * N * COLS;                                             // this thread's plane
+        C v[E];
 #pragma unroll
-                for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
-                __syncthreads();
-                if (has_next) prefetch_line(next, l);
-                if (mode == MODE_COL_INV) LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
-                else LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
-                store_line(item, l, v);
-            }
-            continue;
-        }
-        // 1. forward transforms, parked at own positions
-        for (int l = 0; l < L; ++l) {
-            cp_async_wait_pending(L - 1 - l);
-            __syncthreads();
-            C v[E];
-            C* Sl = Sb + (l * COLS + g) * PS;
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+        for (int m = 0; m < E; ++m) v[m] = Yc[(t + TL * m) * COLS + w];
+        if (mode == MODE_COL_GAMMA) {
+            // forward transforms, Gamma on every position of the item, inverse transforms
             LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
 #pragma unroll
-            for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
-        }
-        // 2. Gamma multiply at own positions
-        {
-            const int64_t inner = (item % cblocks) * COLS + g;
+            for (int m = 0; m < E; ++m) Yc[(t + TL * m) * COLS + w] = v[m];
+            __syncthreads();
+            const int64_t inner0 = (item % cblocks) * COLS;
             const bool two_d = A.line_axis == 1;   // 2-D: inner = kx, line = ky; 3-D z: inner = kx + nx ky
-            const int kx = two_d ? (int)inner : (int)(inner % nx);
-            const int ky0 = two_d ? 0 : (int)(inner / nx);
-#pragma unroll 4
-            for (int m = 0; m < E; ++m) {
-                const int kl = t + TL * m;
-                const int ki[3] = {kx, two_d ? kl : ky0, two_d ? 0 : kl};
+            for (int p = threadIdx.x; p < N * COLS; p += Cfg::THREADS) {
+                const int kl = p / COLS, wc = p % COLS;
+                const int64_t inner = inner0 + wc;
+                const int kx = two_d ? (int)inner : (int)(inner % nx);
+                const int ki[3] = {kx, two_d ? kl : (int)(inner / nx), two_d ? 0 : kl};
                 C q[D];
 #pragma unroll
-                for (int c = 0; c < D; ++c) q[c] = Sb[(c * COLS + g) * PS + kl];
+                for (int cc = 0; cc < D; ++cc) q[cc] = Bi[(cc * N + kl) * COLS + wc];
                 gamma_apply<T, D>(q, ki, A);
 #pragma unroll
-                for (int c = 0; c < D; ++c) Sb[(c * COLS + g) * PS + kl] = q[c];
+                for (int cc = 0; cc < D; ++cc) Bi[(cc * N + kl) * COLS + wc] = q[cc];
             }
-        }
-        // 3. inverse transforms and stores; stage the next item line by line
-        for (int l = 0; l < L; ++l) {
-            C v[E];
-            C* Sl = Sb + (l * COLS + g) * PS;
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
             __syncthreads();
-            if (has_next) prefetch_line(next, l);
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = Yc[(t + TL * m) * COLS + w];
             LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
-            store_line(item, l, v);
+        } else if (mode == MODE_COL_INV) {
+            LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+        } else {
+            LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
         }
+        __syncthreads();   // every thread has read buffer b: refill it
+        if (leader && after < n_items) load_item(after, b);
+        C* dst = A.X + c * A.Ntot + (item / cblocks) * A.outer_stride + (item % cblocks) * COLS + w;
+#pragma unroll
+        for (int m = 0; m < E; ++m) dst[(int64_t)(t + TL * m) * A.ls] = v[m];
     }
-    cp_async_wait_all();
+    if (fault) atomicExch(&A.ctrl->fault, 1);
 }
 
 }  // namespace lsfft
