@@ -5,8 +5,9 @@ fraction on an 8192 x 8192 grid, inclusion conductivities sigma_1 in
 {0.01, 0.1, 10, 100, 1e4}, each solved to a relative sigma_* change of 1e-6
 (three consecutive iterates) with the basic Moulinec-Suquet scheme and with the
 accelerated scheme (Eyre-Milton in the substituted space H'') using the
-paper's pole-interval estimate [alpha, beta] = [1/4, 4]; complex FP32 fields,
-FP64 reductions, trigonometric Green symbol.  Inputs are synthetic and already
+paper's pole-interval estimate [alpha, beta] = [1/4, 4]; FP32 fields (real
+sigma_1: the packed real layout, two half-spectrum planes), FP64 reductions,
+trigonometric Green symbol.  Inputs are synthetic and already
 resident on the device for `value`; `e2e` repeats the step through the C ABI
 from a pinned host mask to pinned host copies of every field E.
 
@@ -74,7 +75,7 @@ def workload_config(args, sigmas):
         "workload": f"2D square array of squares (f=0.25), {args.n}x{args.n}, sigma1 in {list(sigmas)}, "
                     f"MS vs EM-in-H'' (alpha,beta)=(1/4,4), rel. sigma* change {TOL:g} x3, {args.green} Green symbol",
         "n": args.n, "d": 2, "sigma1": list(sigmas), "schemes": list(SCHEMES), "alpha_beta": list(ALPHA_BETA),
-        "tol": TOL, "green": args.green, "fields": "complex FP32, FP64 reductions",
+        "tol": TOL, "green": args.green, "fields": "FP32 (packed real layout: two half-spectrum planes), FP64 reductions",
         "l2": "inputs larger than L2 (state 1 GiB per field at 8192^2)",
     }
 
