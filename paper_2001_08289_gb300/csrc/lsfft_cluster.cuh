@@ -49,8 +49,9 @@ struct CluCfg {
     static constexpr int E = sizeof(T) == 4 ? 16 : 8;
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
     static constexpr int TL = M >= E ? M / E : 1;      // threads per line (only N >= 2048 is launched)
-    static constexpr int THREADS = cmin(512, LINES * TL);
-    static constexpr int G = THREADS / TL;             // lines transformed concurrently
+    static constexpr int COMPUTE = cmin(512, LINES * TL);   // threads that transform and exchange
+    static constexpr int THREADS = COMPUTE + 32;       // + one producer warp for the TMA traffic
+    static constexpr int G = COMPUTE / TL;             // lines transformed concurrently
     static constexpr int SPR = G / W;                  // slots per round
     static constexpr int ROUNDS = LS / (SPR > 0 ? SPR : 1);
     static constexpr int BJ = 256;                     // rows of the inner TMA box dimension
@@ -60,9 +61,11 @@ struct CluCfg {
     // lines w and w + 1 of a warp at equal positions fall into disjoint banks
     static constexpr int XP = roundup16(M + M / 16) + 8;
     static constexpr int Y_BYTES = LS * SLOT_BYTES;
-    static constexpr int SMEM = Y_BYTES + G * XP * CS + 64;   // + two mbarriers
+    static constexpr int SLOT_WARPS = W * TL / 32;     // warps that transform one slot
+    static constexpr int SMEM = Y_BYTES + G * XP * CS + 64;   // + four mbarriers
     static constexpr bool SUPPORTED = N >= 2048 && SMEM <= 227 * 1024 && SPR >= 1 && G == SPR * W &&
-                                      LS % SPR == 0 && M % BJ == 0 && THREADS == G * TL;
+                                      LS % SPR == 0 && M % BJ == 0 && COMPUTE == G * TL &&
+                                      (W * TL) % 32 == 0;
 };
 
 template <typename T, int N>
@@ -81,28 +84,31 @@ col_pass_cluster(const __grid_constant__ PassArgs<T> A) {
     const int q = (int)cluster.block_rank();
     const int64_t cid = blockIdx.x / CL, ncl = gridDim.x / CL;
     C* Y = reinterpret_cast<C*>(smem_raw);             // [LS][M][W]
-    // thread -> (slot within the round, line position t, column w), columns fastest
+    constexpr int COMPUTE = Cfg::COMPUTE;
+    const bool producer = threadIdx.x >= COMPUTE;
+    // transform threads -> (slot within the round, line position t, column w), columns fastest
     const int w = threadIdx.x % W;
     const int t = (threadIdx.x / W) % TL;
-    const int sl = threadIdx.x / (W * TL);
+    const int sl = (threadIdx.x / (W * TL)) % SPR;
     C* Xg = reinterpret_cast<C*>(smem_raw + Cfg::Y_BYTES) + (sl * W + w) * XP;
-    const uint32_t bar0 = smem_u32(smem_raw + Cfg::Y_BYTES + Cfg::G * XP * Cfg::CS);   // bars at bar0, bar0 + 8
+    // mbarriers: full[s] (TMA load landed) at bar0 + 8 s, done[s] (slot transformed) at bar0 + 16 + 8 s
+    const uint32_t bar0 = smem_u32(smem_raw + Cfg::Y_BYTES + Cfg::G * XP * Cfg::CS);
     const CUtensorMap* map = &A.tmap;
     // n_inner need not be a multiple of W (the half-spectrum planes hold
     // n_x/2 + 1 columns within a padded pitch): the last item runs into padding
     const int64_t n_items = (A.n_inner + W - 1) / W;
-    const bool leader = threadIdx.x == 0;
+    const bool leader = threadIdx.x == COMPUTE;         // lane 0 of the producer warp
 
     C* Yr[CL];                                          // the item buffers of every block of the cluster
 #pragma unroll
     for (int p = 0; p < CL; ++p) Yr[p] = cluster.map_shared_rank(Y, p);
 
-    auto load_slot = [&](int64_t item, int s) {         // leader only
+    auto load_slot = [&](int64_t item, int s) {         // producer only
         const uint32_t bar = bar0 + 8 * s;
         mbar_expect_tx(bar, Cfg::SLOT_BYTES);
         tma_load_5d(smem_u32(Y) + s * Cfg::SLOT_BYTES, map, (int)(item * W * EPC), q, 0, 0, s, bar);
     };
-    auto store_slot = [&](int64_t item, int s) {        // leader only
+    auto store_slot = [&](int64_t item, int s) {        // producer only
         tma_store_5d(map, (int)(item * W * EPC), q, 0, 0, s, smem_u32(Y) + s * Cfg::SLOT_BYTES);
         bulk_commit();
     };
@@ -121,93 +127,102 @@ col_pass_cluster(const __grid_constant__ PassArgs<T> A) {
     };
     static_assert(M % BJ == 0, "rows of a block must fill whole TMA boxes");
 
-    if (leader) {
-        mbar_init(bar0, 1);
-        mbar_init(bar0 + 8, 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < LS; ++s) {
+            mbar_init(bar0 + 8 * s, 1);
+            mbar_init(bar0 + 16 + 8 * s, Cfg::SLOT_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int64_t item = cid;
-    if (leader && item < n_items)
-        for (int s = 0; s < LS; ++s) load_slot(item, s);
     bool fault = false;
-    for (uint32_t it = 0; item < n_items; item += ncl, ++it) {
-        const int64_t next = item + ncl;
-        // 1. local forward M-point transforms in place; round rd covers slots
-        //    rd*SPR .. rd*SPR + SPR - 1 and starts when they have landed
-        for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
-            const int s = rd * SPR + sl;
-            if (!mbar_wait(bar0 + 8 * s, it & 1u, MBAR_WAIT_LIMIT)) fault = true;
-            C* Ys = Y + s * M * W;
-            C v[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Ys[(t + TL * m) * W + w];
-            LineFFT<T, M, E, Cfg::RMAX, false>::run(v, Xg, t, A.tw, CL);
-#pragma unroll
-            for (int m = 0; m < E; ++m) Ys[(t + TL * m) * W + w] = v[m];
-        }
-        cluster.sync();
-        // 2. exchange: combine, Gamma, inverse combine over the owned k range
-        for (int idx = threadIdx.x; idx < W * KQ; idx += Cfg::THREADS) {
-            const int wc = idx % W, k = q * KQ + idx / W;
-            C tw[CL];
-            twiddles(k, tw);
-            C x[LS][CL];
-#pragma unroll
-            for (int s = 0; s < LS; ++s) {
-                C y[CL];
-#pragma unroll
-                for (int p = 0; p < CL; ++p) y[p] = cmul(Yr[p][(s * M + k) * W + wc], tw[p]);
-                dft<CL, false, false>(y);   // x[m] = sum_p y[p] W_CL^(p m)
-#pragma unroll
-                for (int m = 0; m < CL; ++m) x[s][m] = y[m];
-            }
-            const int kx = (int)(item * W + wc);
-#pragma unroll
-            for (int m = 0; m < CL; ++m) {
-                C vq[2] = {x[0][m], x[1][m]};
-                const int ki[3] = {kx, k + M * m, 0};
-                gamma_apply<T, 2>(vq, ki, A);
-                x[0][m] = vq[0];
-                x[1][m] = vq[1];
-            }
-#pragma unroll
-            for (int s = 0; s < LS; ++s) {
-                // inverse CL-point DFT over m, then * conj W_N^(p k)
-                dft<CL, true, false>(x[s]);
-#pragma unroll
-                for (int p = 0; p < CL; ++p) Yr[p][(s * M + k) * W + wc] = cmulc(x[s][p], tw[p]);
-            }
-        }
-        cluster.sync();
-        // 3. local inverse M-point transforms in place.  After each round its
-        //    slots go out by TMA store; the slots of the round before are
-        //    restaged for the next item once their store has read them.
-        for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
-            const int s = rd * SPR + sl;
-            C* Ys = Y + s * M * W;
-            C v[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Ys[(t + TL * m) * W + w];
-            LineFFT<T, M, E, Cfg::RMAX, true>::run(v, Xg, t, A.tw, CL);
-#pragma unroll
-            for (int m = 0; m < E; ++m) Ys[(t + TL * m) * W + w] = v[m];
-            fence_proxy_async_smem();   // the TMA store reads what the threads wrote
-            __syncthreads();
+    int64_t item = cid;
+    if (producer) {
+        // The producer warp: stores each slot as soon as its transforms are done,
+        // and fetches the next item's tile into it once the store has read it.
+        if (leader && item < n_items)
+            for (int s = 0; s < LS; ++s) load_slot(item, s);
+        for (uint32_t it = 0; item < n_items; item += ncl, ++it) {
+            const int64_t next = item + ncl;
+            cluster.sync();   // the transform threads' first barrier of this item
+            cluster.sync();   // ... and their second
             if (leader) {
-                for (int j = 0; j < SPR; ++j) store_slot(item, rd * SPR + j);
-                if (rd > 0 && next < n_items) {
-                    bulk_wait_read(1);   // the store of round rd - 1 has read its slots
-                    for (int j = 0; j < SPR; ++j) load_slot(next, (rd - 1) * SPR + j);
+                for (int s = 0; s < LS; ++s) {
+                    if (!mbar_wait(bar0 + 16 + 8 * s, it & 1u, MBAR_WAIT_LIMIT)) fault = true;
+                    store_slot(item, s);
+                    bulk_wait_read(0);
+                    if (next < n_items) load_slot(next, s);
                 }
             }
+            __syncwarp();
         }
-        if (leader && next < n_items) {
-            bulk_wait_read(0);
-            for (int j = 0; j < SPR; ++j) load_slot(next, (Cfg::ROUNDS - 1) * SPR + j);
+        if (leader) bulk_wait_all();
+    } else {
+        for (uint32_t it = 0; item < n_items; item += ncl, ++it) {
+            // 1. local forward M-point transforms in place; round rd covers slots
+            //    rd*SPR .. rd*SPR + SPR - 1 and starts when they have landed
+            for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
+                const int s = rd * SPR + sl;
+                if (!mbar_wait(bar0 + 8 * s, it & 1u, MBAR_WAIT_LIMIT)) fault = true;
+                C* Ys = Y + s * M * W;
+                C v[E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = Ys[(t + TL * m) * W + w];
+                LineFFT<T, M, E, Cfg::RMAX, false, false, COMPUTE>::run(v, Xg, t, A.tw, CL);
+#pragma unroll
+                for (int m = 0; m < E; ++m) Ys[(t + TL * m) * W + w] = v[m];
+            }
+            cluster.sync();
+            // 2. exchange: combine, Gamma, inverse combine over the owned k range
+            for (int idx = threadIdx.x; idx < W * KQ; idx += COMPUTE) {
+                const int wc = idx % W, k = q * KQ + idx / W;
+                C tw[CL];
+                twiddles(k, tw);
+                C x[LS][CL];
+#pragma unroll
+                for (int s = 0; s < LS; ++s) {
+                    C y[CL];
+#pragma unroll
+                    for (int p = 0; p < CL; ++p) y[p] = cmul(Yr[p][(s * M + k) * W + wc], tw[p]);
+                    dft<CL, false, false>(y);   // x[m] = sum_p y[p] W_CL^(p m)
+#pragma unroll
+                    for (int m = 0; m < CL; ++m) x[s][m] = y[m];
+                }
+                const int kx = (int)(item * W + wc);
+#pragma unroll
+                for (int m = 0; m < CL; ++m) {
+                    C vq[2] = {x[0][m], x[1][m]};
+                    const int ki[3] = {kx, k + M * m, 0};
+                    gamma_apply<T, 2>(vq, ki, A);
+                    x[0][m] = vq[0];
+                    x[1][m] = vq[1];
+                }
+#pragma unroll
+                for (int s = 0; s < LS; ++s) {
+                    // inverse CL-point DFT over m, then * conj W_N^(p k)
+                    dft<CL, true, false>(x[s]);
+#pragma unroll
+                    for (int p = 0; p < CL; ++p) Yr[p][(s * M + k) * W + wc] = cmulc(x[s][p], tw[p]);
+                }
+            }
+            cluster.sync();
+            // 3. local inverse M-point transforms in place; each slot is handed to
+            //    the producer warp when its warps are done with it
+            for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
+                const int s = rd * SPR + sl;
+                C* Ys = Y + s * M * W;
+                C v[E];
+#pragma unroll
+                for (int m = 0; m < E; ++m) v[m] = Ys[(t + TL * m) * W + w];
+                LineFFT<T, M, E, Cfg::RMAX, true, false, COMPUTE>::run(v, Xg, t, A.tw, CL);
+#pragma unroll
+                for (int m = 0; m < E; ++m) Ys[(t + TL * m) * W + w] = v[m];
+                fence_proxy_async_smem();   // the TMA store reads what the threads wrote
+                __syncwarp();
+                if ((threadIdx.x & 31) == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar0 + 16 + 8 * s) : "memory");
+            }
         }
     }
-    if (leader) bulk_wait_all();
     if (fault) atomicExch(&A.ctrl->fault, 1);
     cluster.sync();   // no block leaves while a peer may still address its shared memory
 }

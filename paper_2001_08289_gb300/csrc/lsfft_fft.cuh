@@ -173,7 +173,16 @@ __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
 template <int N> struct LinePad { static constexpr int size = N + N / 16 + 1; };
 
-template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false>
+// Barrier over the threads that run line transforms: the whole block, or (SYNC
+// > 0) the first SYNC threads on hardware barrier 1, when other warps of the
+// block do other work.
+template <int SYNC>
+__device__ __forceinline__ void line_sync() {
+    if constexpr (SYNC == 0) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"n"(SYNC) : "memory");
+}
+
+template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false, int SYNC = 0>
 struct LineFFT {
     using C = cx<T>;
     static constexpr int TL = N / E;   // threads per line
@@ -225,7 +234,7 @@ struct LineFFT {
         constexpr bool LAST = (NS * R == N);
         constexpr int B = E / R;
         static_assert(E % R == 0, "radix must divide E");
-        if constexpr (!LAST) __syncthreads();   // previous readers of sm are done
+        if constexpr (!LAST) line_sync<SYNC>();   // previous readers of sm are done
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int j = t + TL * i;
@@ -244,15 +253,16 @@ struct LineFFT {
             }
         }
         if constexpr (!LAST) {
-            __syncthreads();
+            line_sync<SYNC>();
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m)];
             stage<NS * R>(v, sm, t, tw, tws);
         }
     }
 
-    // Must be called by every thread of the block (it contains __syncthreads()
-    // whenever N > RMAX); threads of inactive lines pass dummy data.  FP64:
+    // Must be called by every thread of the block (or of the SYNC transform
+    // threads: it contains barriers whenever N > RMAX); threads of inactive lines
+    // pass dummy data.  FP64:
     // `tw` holds W_L^k of a length L = N * tws (tws = 1 unless the line is a
     // decimated part of a longer one).
     __device__ __forceinline__ static void run(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
