@@ -235,13 +235,32 @@ struct LineFFT {
         constexpr int B = E / R;
         static_assert(E % R == 0, "radix must divide E");
         if constexpr (!LAST) line_sync<SYNC>();   // previous readers of sm are done
+        // A last stage with several butterflies per thread (R < E): butterfly i has
+        // j = t + TL i < NS, so its twiddles W_N^((t + TL i) r) = W_N^(t r) W_E^(i r)
+        // share the powers of W_N^t and differ by exact 16th roots of unity
+        // (FP32; FP64 reads its table).
+        constexpr bool SHARED_TW = LAST && B > 1 && NS > 1 && sizeof(T) == 4 && (16 % E == 0);
+        C pw[R];
+        if constexpr (SHARED_TW) {
+            float s, c;
+            sincospif(2.0f * (float)t / (float)N, &s, &c);
+            pw[0] = mkc((T)1, (T)0);
+            pw[1] = mkc(c, INV ? s : -s);
+#pragma unroll
+            for (int r = 2; r < R; ++r) pw[r] = cmul(pw[r - 1], pw[1]);
+        }
 #pragma unroll
         for (int i = 0; i < B; ++i) {
             const int j = t + TL * i;
             C a[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) a[r] = v[i + r * B];
-            if constexpr (NS > 1) twiddle<R>(a, j % NS, NS * R, tw, tws);
+            if constexpr (SHARED_TW) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) a[r] = cmul(a[r], mul_root16<INV>(pw[r], (i * r * (16 / E)) & 15));
+            } else if constexpr (NS > 1) {
+                twiddle<R>(a, j % NS, NS * R, tw, tws);
+            }
             dft<R, INV, PAIRED>(a);
             if constexpr (LAST) {
 #pragma unroll
