@@ -189,6 +189,16 @@ int lsfft_solve_batch(int njobs, const lsfft_job *jobs, lsfft_result **results, 
  * entries. */
 int lsfft_set_sigma_field(lsfft_grid *grid, const lsfft_c128 *sigma, int on_device, lsfft_c128 sigma0);
 
+/* Fault injection for tests (the paper has no counterpart).  kind 1: the
+ * strided passes of later solves on this grid announce 16 more bytes to each
+ * TMA completion barrier than the copy delivers, and every barrier wait gives
+ * up after 2e7 clock cycles instead of about two seconds: each wait runs out,
+ * the kernel records a fault and completes, and lsfft_solve returns
+ * LSFFT_ECUDA ("a bounded wait ... gave up") with no result; the GPU context
+ * stays usable.  kind 0 restores normal operation.  Waits for any pending work
+ * of the grid first.  EINVAL for a null grid or another kind. */
+int lsfft_debug_inject(lsfft_grid *grid, int kind);
+
 /* Gradient of sigma_* for the field of `res` (a result of this grid): the first
  * variation of the energy <sigma E.E> = sigma_* |e|^2 of Eq. J12/J13 (E.E
  * bilinear, no conjugation, so complex conductivities are covered) gives

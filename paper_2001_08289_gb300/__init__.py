@@ -28,7 +28,7 @@ __all__ = [
     "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
     "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
     "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "lsfft_solve_batch", "solve_batch",
-    "lsfft_substitution_rates",
+    "lsfft_substitution_rates", "lsfft_debug_inject",
     "make_opts",
     "SCHEMES", "GREENS",
 ]
@@ -118,6 +118,7 @@ def load_library():
     lib.lsfft_tridiag_gauss.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.lsfft_set_sigma_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int, _C128]
+    lib.lsfft_debug_inject.argtypes = [C.c_void_p, C.c_int]
     lib.lsfft_solve_batch.argtypes = [C.c_int, C.POINTER(_Job), C.POINTER(C.POINTER(_Result)), C.POINTER(C.c_int)]
     lib.lsfft_substitution_rates.argtypes = [_C128, C.c_double, C.c_double, C.POINTER(C.c_double),
                                              C.POINTER(C.c_double)]
@@ -286,6 +287,10 @@ def lsfft_set_sigma_field(grid: int, sigma_ptr, on_device: bool, sigma0: complex
     s0 = complex(sigma0)
     _check(load_library().lsfft_set_sigma_field(C.c_void_p(grid), C.c_void_p(sigma_ptr) if sigma_ptr else None,
                                                 int(bool(on_device)), _C128(s0.real, s0.imag)))
+
+
+def lsfft_debug_inject(grid: int, kind: int) -> None:
+    _check(load_library().lsfft_debug_inject(C.c_void_p(grid), int(kind)))
 
 
 def lsfft_gradient(grid: int, res, e, grad_ptr=None):

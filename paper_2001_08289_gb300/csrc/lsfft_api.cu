@@ -110,6 +110,8 @@ struct lsfft_grid {
     bool sig_real = false;
     double sigma0_user[2] = {0.0, 0.0};
     int bench_prec = -1;            // precision of the state set up by lsfft_prepare (-1: none)
+    int inject_tx = 0;              // test hook (lsfft_debug_inject): TMA bytes announced, never sent
+    long long wait_limit = MBAR_WAIT_LIMIT;
     int bench_st = 0;
     std::map<GraphKey, cudaGraphExec_t> graphs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -494,6 +496,8 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
     A.ctrl = g->ctrl_dev;
     A.partials = g->partials;
     for (int a = 0; a < 3; ++a) A.fd[a] = a < g->d ? (const cx<T>*)g->fd[a][p] : nullptr;
+    A.wait_limit = g->wait_limit;
+    A.extra_tx = g->inject_tx;
     A.Ntot = g->N;
     A.hp = half_pitch(g->n[0]);
     A.Nh = (g->N / g->n[0]) * A.hp;
@@ -1315,6 +1319,18 @@ int lsfft_lanczos_hull(lsfft_grid* g, const double* e, int green, int precision,
         if (nodes) nodes[i] = th[i];
         if (weights) weights[i] = w2[i];
     }
+    return LSFFT_OK;
+}
+
+int lsfft_debug_inject(lsfft_grid* g, int kind) {
+    if (!g || kind < 0 || kind > 1) {
+        g_last_error = "lsfft_debug_inject: null grid or unknown kind";
+        return LSFFT_EINVAL;
+    }
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    clear_graphs(g);
+    g->inject_tx = kind == 1 ? 16 : 0;
+    g->wait_limit = kind == 1 ? 20000000LL : MBAR_WAIT_LIMIT;
     return LSFFT_OK;
 }
 

@@ -105,7 +105,7 @@ col_pass_cluster(const __grid_constant__ PassArgs<T> A) {
 
     auto load_slot = [&](int64_t item, int s) {         // producer only
         const uint32_t bar = bar0 + 8 * s;
-        mbar_expect_tx(bar, Cfg::SLOT_BYTES);
+        mbar_expect_tx(bar, Cfg::SLOT_BYTES + A.extra_tx);
         tma_load_5d(smem_u32(Y) + s * Cfg::SLOT_BYTES, map, (int)(item * W * EPC), q, 0, 0, s, bar);
     };
     auto store_slot = [&](int64_t item, int s) {        // producer only
@@ -148,7 +148,7 @@ col_pass_cluster(const __grid_constant__ PassArgs<T> A) {
             cluster.sync();   // ... and their second
             if (leader) {
                 for (int s = 0; s < LS; ++s) {
-                    if (!mbar_wait(bar0 + 16 + 8 * s, it & 1u, MBAR_WAIT_LIMIT)) fault = true;
+                    if (!mbar_wait(bar0 + 16 + 8 * s, it & 1u, A.wait_limit)) fault = true;
                     store_slot(item, s);
                     bulk_wait_read(0);
                     if (next < n_items) load_slot(next, s);
@@ -163,7 +163,7 @@ col_pass_cluster(const __grid_constant__ PassArgs<T> A) {
             //    rd*SPR .. rd*SPR + SPR - 1 and starts when they have landed
             for (int rd = 0; rd < Cfg::ROUNDS; ++rd) {
                 const int s = rd * SPR + sl;
-                if (!mbar_wait(bar0 + 8 * s, it & 1u, MBAR_WAIT_LIMIT)) fault = true;
+                if (!mbar_wait(bar0 + 8 * s, it & 1u, A.wait_limit)) fault = true;
                 C* Ys = Y + s * M * W;
                 C v[E];
 #pragma unroll

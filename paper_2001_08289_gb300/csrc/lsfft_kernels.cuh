@@ -401,7 +401,9 @@ struct PassArgs {
     int grid_blocks;          // persistent grid size chosen by the host
     int packed;               // packed real layout (2-D row pass only; the strided pass sees two planes)
     KConst<T> k;
-    CUtensorMap tmap;         // cluster strided pass: TMA view of the two planes (encoded by the host)
+    long long wait_limit;     // bound of every mbarrier wait, in clock cycles
+    int extra_tx;             // test hook: bytes announced but never delivered (0 in normal runs)
+    CUtensorMap tmap;         // strided passes: TMA view of the planes (encoded by the host)
 };
 
 // ---------------------------------------------------------------------------
@@ -783,7 +785,7 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
 
     auto load_item = [&](int64_t item, int b) {   // leader only
         const uint32_t bar = bar0 + 8 * b;
-        mbar_expect_tx(bar, Cfg::ITEM_BYTES);
+        mbar_expect_tx(bar, Cfg::ITEM_BYTES + A.extra_tx);
         tma_load_5d(smem_u32(Bf) + b * Cfg::ITEM_BYTES, &A.tmap, (int)((item % cblocks) * COLS * EPC), 0, 0,
                     (int)(item / cblocks), 0, bar);
     };
@@ -803,7 +805,7 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
     for (uint32_t it = 0; item < n_items; item += A.grid_blocks, ++it) {
         const int b = it & 1;
         const int64_t after = item + 2 * (int64_t)A.grid_blocks;   // the next item for this buffer
-        if (!mbar_wait(bar0 + 8 * b, (it >> 1) & 1u, MBAR_WAIT_LIMIT)) fault = true;
+        if (!mbar_wait(bar0 + 8 * b, (it >> 1) & 1u, A.wait_limit)) fault = true;
         C* Bi = Bf + (size_t)b * D * N * COLS;
         C* Yc = Bi + c * N * COLS;                                             // this thread's plane
         C v[E];

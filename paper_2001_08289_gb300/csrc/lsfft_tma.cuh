@@ -59,6 +59,6 @@ __device__ __forceinline__ void bulk_wait_read(int n) {
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-constexpr long long MBAR_WAIT_LIMIT = 4000000000LL;   // clock cycles (about two seconds)
+constexpr long long MBAR_WAIT_LIMIT = 4000000000LL;   // default bound of a wait: clock cycles (about two seconds)
 
 }  // namespace lsfft

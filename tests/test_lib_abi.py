@@ -76,3 +76,8 @@ def test_tridiag_gauss_matches_dense_eigh(lib):
         np.testing.assert_allclose(nodes[order], w, atol=1e-12)
         np.testing.assert_allclose(first2[order], V[0] ** 2, atol=1e-10)
         assert abs(first2.sum() - 1.0) < 1e-12
+
+
+def test_debug_inject_rejects_null_grid_without_gpu(lib):
+    lib.lsfft_debug_inject.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.lsfft_debug_inject(None, 1) == 1
