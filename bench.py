@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--pass-reps", type=int, default=20)
     p.add_argument("--workload", default="square2d",
-                   choices=("square2d", "lattice64", "cube3d", "sweep", "adjoint", "fig5", "passes"),
+                   choices=("square2d", "lattice64", "cube3d", "sweep", "adjoint", "fig5", "passes", "cufft",
+                            "precision"),
                    help="square2d (default): the headline 2-D square-array sweep; the others measure the "
                         "64^2 FP64 lattice, the 3-D cubic arrays, the batched complex-sigma_1 sweep and the "
                         "adjoint (gradient) configuration, one JSON line each")
@@ -639,6 +640,90 @@ def run_adjoint(args):
           fd_median_rel_err=float(np.median(errs)))
 
 
+def run_cufft(args):
+    """Comparison only: the same Moulinec-Suquet update on the same 8192^2 square
+    array written with torch.fft (cuFFT real-to-complex transforms) and torch
+    elementwise kernels, FP32, trig symbol, sigma_1 = 10: tau = (sigma/sigma_0 - 1) E,
+    E^ = -Gamma tau^ (zero mode N e, Nyquist lines zero), E = inverse FFT, and the
+    average <sigma E> per update.  Fixed iteration count, CUDA events."""
+    torch, L = _gpu_setup()
+    n = args.n
+    dev = torch.device("cuda", 0)
+    mask = torch.from_numpy(square_array_mask(n)).to(dev)
+    s1, s0 = 10.0, (10.0 + 1.0) / 2
+    a = torch.where(mask != 0, torch.tensor(s1 / s0 - 1, device=dev), torch.tensor(1 / s0 - 1, device=dev))
+    sig = torch.where(mask != 0, torch.tensor(s1, device=dev), torch.tensor(1.0, device=dev))
+    ky = torch.fft.fftfreq(n, d=1.0 / n, device=dev).round().view(n, 1)
+    kx = torch.arange(n // 2 + 1, device=dev, dtype=torch.float32).view(1, n // 2 + 1)
+    nyq = (ky == -(n // 2)) | (kx == n // 2)
+    k2 = kx * kx + ky * ky
+    inv = torch.where((k2 > 0) & ~nyq, 1.0 / k2.clamp(min=1.0), torch.zeros_like(k2))
+    E = torch.zeros((2, n, n), device=dev, dtype=torch.float32)
+    E[0] = 1.0
+
+    def update(E):
+        T = torch.fft.rfft2(a * E)
+        proj = (kx * T[0] + ky * T[1]) * inv
+        Eh = torch.stack((-kx * proj, -ky * proj))
+        Eh[0, 0, 0] = n * n * 1.0
+        Eh[1, 0, 0] = 0.0
+        E = torch.fft.irfft2(Eh, s=(n, n))
+        sigma_k = (sig * E[0]).mean()
+        return E, sigma_k
+
+    iters = 30
+    for _ in range(3):
+        E, sk = update(E)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(iters):
+        E, sk = update(E)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / iters
+    _line("voxel-iters/s (torch.fft / cuFFT comparison, MS update)", n * n / (ms / 1e3), UNIT, args,
+          {"workload": f"{n}x{n} square array, sigma1 = 10, MS update with torch.fft.rfft2/irfft2 (cuFFT) and torch "
+                       "elementwise kernels, FP32, trig symbol; comparison only, not the library's path", "n": n},
+          dtype="f32", ms_per_update=round(ms, 4), sigma_k=float(sk))
+
+
+def run_precision(args):
+    """FP32 fields with FP64 reductions against an all-FP64 GPU run on the 2048^2
+    square array (sigma_1 in the 2-D sweep, MS and EM in H'' on [1/4, 4], trig):
+    sigma_* and E differences, and the iterations and wall time until sigma_k is
+    within 1e-6 of the FP64 run's converged value (time to a true tolerance)."""
+    torch, L = _gpu_setup()
+    n = args.n if args.n <= 4096 else 2048
+    mask = square_array_mask(n)
+    e = [1.0, 0.0]
+    out = {}
+    with L.Grid(mask) as g:
+        for s1 in (0.01, 0.1, 10.0, 100.0, 1e4):
+            ref = g.solve(s1, e, scheme="em_sub", precision="fp64", tol=1e-12, max_iter=2000, alpha=0.25, beta=4.0)
+            s_ref = ref.sigma_star
+            E_ref = ref.field_numpy()
+            ref.free()
+            for sch in SCHEMES:
+                row = {}
+                for prec in ("fp32", "fp64"):
+                    r = g.solve(s1, e, scheme=sch, precision=prec, tol=TOL, max_iter=500, alpha=0.25, beta=4.0)
+                    err = np.abs(r.hist_sigma - s_ref) / abs(s_ref)
+                    hit = int(np.argmax(err <= 1e-6)) if np.any(err <= 1e-6) else None
+                    Ef = r.field_numpy().astype(np.complex128)
+                    row[prec] = {"iters": r.iterations, "status": r.status, "ms": round(r.solve_ms, 3),
+                                 "rel_err_sigma_vs_fp64_converged": float(abs(r.sigma_star - s_ref) / abs(s_ref)),
+                                 "rel_l2_E_vs_fp64_converged": float(np.linalg.norm(Ef - E_ref) / np.linalg.norm(E_ref)),
+                                 "iters_to_true_1e-6": hit,
+                                 "ms_to_true_1e-6": None if hit is None else round(r.solve_ms * (hit + 1) / (r.iterations + 1), 3)}
+                    r.free()
+                out[f"{s1:g}|{sch}"] = row
+    _line("sigma_* and E agreement of FP32 fields with an all-FP64 run; time to a true 1e-6", n * n, "voxels", args,
+          {"workload": f"{n}x{n} square array, sigma1 in [0.01, 0.1, 10, 100, 1e4], MS and EM in H'' on [1/4, 4], "
+                       "trig symbol, stop at relative change 1e-6; reference: EM in H'' in FP64 to 1e-12", "n": n},
+          dtype="f32 and f64", results=out)
+
+
 def run_passes(args):
     """Pass timing alone (the unit the profiles capture): after one lsfft_prepare per
     scheme, `--pass-reps` launches of the row pass, then of the strided pass(es), on
@@ -739,7 +824,7 @@ def main():
         run_ours(args, sigmas)
     else:
         {"lattice64": run_lattice64, "cube3d": run_cube3d, "sweep": run_sweep, "adjoint": run_adjoint,
-         "fig5": run_fig5, "passes": run_passes}[
+         "fig5": run_fig5, "passes": run_passes, "cufft": run_cufft, "precision": run_precision}[
             args.workload](args)
 
 

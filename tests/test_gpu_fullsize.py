@@ -1,0 +1,91 @@
+"""Parity at the full sizes of the square-array sweep, in the configuration the
+benchmark times (FP32 fields with FP64 reductions, and FP64): element by element
+against the FP64 oracle on the 2048 x 2048 grid, and on the 8192 x 8192 grid
+through properties that hold at any size plus oracle values computed point by
+point."""
+import numpy as np
+import pytest
+
+from oracle import constants as K
+from oracle import schemes as S
+from synth import square_array_mask
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = {"fp64": (1e-10, 1e-10), "fp32": (1e-5, 1e-4)}
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2001_08289_gb300 as lib
+    from paper_2001_08289_gb300 import build
+
+    build.build()
+    lib.load_library()
+    return lib
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("s1,scheme", [(10.0, "ms"), (10.0, "em_sub"), (0.01, "em_sub"), (1e4, "ms")])
+def test_parity_2048_square_array(L, prec, s1, scheme):
+    n, iters = 2048, 4
+    mask = square_array_mask(n)
+    e = np.array([1.0, 0.0])
+    with L.Grid(mask) as g:
+        r = g.solve(s1, e, scheme=scheme, precision=prec, tol=0.0, max_iter=iters, alpha=0.25, beta=4.0)
+        assert r.packed
+        E = r.field_numpy()
+    ref = S.solve(S.Problem(mask, s1, e, "trig"), scheme, alpha=0.25, beta=4.0, tol=0.0, max_iter=iters)
+    st, et = TOL[prec]
+    assert np.max(np.abs(r.hist_sigma - ref.hist_sigma) / np.abs(ref.hist_sigma)) < st
+    assert np.linalg.norm(E - ref.E) / np.linalg.norm(ref.E) < et
+
+
+def test_8192_first_update_sampled_and_invariants(L):
+    """One MS update from E = e on the 8192^2 square array (FP32, the benchmark's
+    layout): <E> = e exactly, sigma_1 of the first iterate and E at sampled voxels
+    against the oracle evaluated point by point (the square array's tau is
+    separable, so tau^ is an outer product of two 1-D transforms), and a converged
+    solve with both schemes giving the same sigma_*."""
+    n = 8192
+    mask = square_array_mask(n)
+    s1 = 10.0
+    e = np.array([1.0, 0.0])
+    with L.Grid(mask) as g:
+        r = g.solve(s1, e, scheme="ms", precision="fp32", tol=0.0, max_iter=1)
+        E = r.field_numpy()
+        mean_E = r.mean_E
+        r.free()
+        rm = g.solve(s1, e, scheme="ms", precision="fp32", tol=1e-6, max_iter=500)
+        re_ = g.solve(s1, e, scheme="em_sub", precision="fp32", tol=1e-6, max_iter=500, alpha=0.25, beta=4.0)
+        assert rm.status == L.OK and re_.status == L.OK
+        assert abs(rm.sigma_star - re_.sigma_star) < 3e-5 * abs(re_.sigma_star)
+    assert abs(mean_E[0] - 1.0) < 1e-6 and abs(mean_E[1]) < 1e-6
+    # oracle first update: E1 = e - IDFT(Gamma(k) tau^(k)), tau = (sigma/sigma_0 - 1) e_x chi-pattern
+    s0 = K.ms_sigma0(s1)
+    a_in, a_out = s1 / s0 - 1.0, 1.0 / s0 - 1.0
+    ind = np.zeros(n)
+    ind[n // 4: 3 * n // 4] = 1.0
+    # tau_x(x, y) = a_out + (a_in - a_out) ind(x) ind(y): separable up to the constant
+    f = np.fft.fft(ind)
+    k = np.fft.fftfreq(n, d=1.0 / n).round()
+    nyq = k == -(n // 2)
+    kx, ky = k[None, :], k[:, None]
+    k2 = kx * kx + ky * ky
+    act = (k2 > 0) & ~nyq[None, :] & ~nyq[:, None]
+    T = np.where(act, (a_in - a_out) * np.outer(f, f) / np.where(k2 > 0, k2, 1.0), 0.0)   # [ky, kx]
+    Mx = T * (kx * kx)
+    My = T * (ky * kx)
+    del T
+    rng = np.random.default_rng(7)
+    for (y, x) in rng.integers(0, n, size=(12, 2)):
+        # E1_c(x, y) = e_c - (1/N) sum_k Gamma_cx(k) tau^_x(k) exp(2 pi i k.x / n), k != 0
+        px = np.exp(2j * np.pi * k * x / n)
+        py = np.exp(2j * np.pi * k * y / n)
+        ex = 1.0 - (py @ (Mx @ px)).real / (n * n)
+        ey = -(py @ (My @ px)).real / (n * n)
+        assert abs(E[0, y, x] - ex) < 2e-5 * max(1.0, abs(ex)), (y, x, E[0, y, x], ex)
+        assert abs(E[1, y, x] - ey) < 2e-5, (y, x, E[1, y, x], ey)
