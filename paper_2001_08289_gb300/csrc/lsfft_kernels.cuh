@@ -473,6 +473,138 @@ row_pass(const PassArgs<T> A) {
         acc[i] = tsum;
     };
 
+    // Packed real layout: the line stays in registers from the join of the half
+    // spectra (Z(k) = X(k) + i Y(k) for k <= n/2, conj(X(n-k)) + i conj(Y(n-k))
+    // above) through the inverse DFT, the scheme update and the forward DFT to
+    // their split (X = (Z(k) + conj Z(n-k))/2, Y = (Z(k) - conj Z(n-k))/(2i)), and
+    // the next item is staged as soon as the join has read this one.
+    auto packed_item = [&](int64_t row, bool active, int64_t base, int64_t next, bool has_next) {
+        cp_async_wait_all();
+        __syncthreads();
+        C v[E];
+        uint32_t incb = 0;   // phase of the thread's points, read before the mask is restaged
+#pragma unroll
+        for (int m = 0; m < E; ++m) incb |= (Mb[g * N + t + TL * m] != 0 ? 1u : 0u) << m;
+        if (mode == MODE_ROW_FIRST) {
+            // the first pass starts from Q = iq e (or the per-voxel reference)
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                T qv;
+                if (A.sigma)
+                    qv = A.k.scheme == SCHEME_EM ? A.sigma[base + t + TL * m].x + A.k.s0.x : (T)1;
+                else
+                    qv = (incb >> m) & 1u ? A.k.iq_in.x : A.k.iq_out.x;
+                v[m] = mkc(qv * A.k.e[0], qv * A.k.e[1]);
+            }
+            __syncthreads();
+        } else {
+            const C* Hx = Sb + g * PS;
+            const C* Hy = Sb + (LPB + g) * PS;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int k = t + TL * m;
+                if (k <= N / 2) {
+                    const C x = Hx[k], y = Hy[k];
+                    v[m] = mkc(x.x - y.y, x.y + y.x);
+                } else {
+                    const C x = Hx[N - k], y = Hy[N - k];
+                    v[m] = mkc(x.x + y.y, y.x - x.y);
+                }
+            }
+            LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+            if constexpr (N <= Cfg::RMAX) __syncthreads();   // (a one-stage transform has no barrier)
+        }
+        // every thread has read the staging buffers: stage the next item
+        if (has_next)
+            for (int l = 0; l < 2; ++l) prefetch_line(next, l);
+
+        if (active) {
+            T sE[2] = {0, 0}, sJ[2] = {0, 0}, sE2 = 0;
+            const bool wst = mode != MODE_ROW_OUTPUT;
+            const bool outm = mode == MODE_ROW_OUTPUT;
+            auto points = [&](auto tag) {
+                constexpr int SCH = decltype(tag)::value;
+                constexpr bool SUB = SCH == SCHEME_MS_SUB || SCH == SCHEME_EM_SUB;
+                // in batches of HB points: S (T) of the phase-1 points first, so
+                // that their global loads are in flight together (fully unrolled:
+                // v is indexed by compile-time positions only)
+                constexpr int HB = (sizeof(T) == 4 ? 4 : 2) < E ? (sizeof(T) == 4 ? 4 : 2) : E;
+#pragma unroll
+                for (int m0 = 0; m0 < E; m0 += HB) {
+                    C sv[HB], tv[HB];
+#pragma unroll
+                    for (int h = 0; h < HB; ++h) {
+                        const int pos = t + TL * (m0 + h);
+                        const bool inc = (incb >> (m0 + h)) & 1u;
+                        sv[h] = tv[h] = mkc((T)0, (T)0);
+                        if constexpr (SUB) {
+                            if (inc) sv[h] = A.S[base + pos];
+                        }
+                        if constexpr (SCH == SCHEME_EM_SUB) {
+                            if (inc) tv[h] = A.Tf[base + pos];
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < HB; ++h) {
+                        const int m = m0 + h;
+                        const int64_t idx = base + t + TL * m;
+                        const bool inc = (incb >> m) & 1u;
+                        C z = v[m], Ez, Jz;
+                        if (!SUB && A.sigma)
+                            pointwise_field_packed<T>(A.k, z, A.sigma[idx].x, Ez, Jz);
+                        else
+                            pointwise_packed<T, SCH>(A.k, z, inc, sv[h], tv[h], Ez, Jz);
+                        if constexpr (SUB) {
+                            if (inc && wst) {
+                                A.S[idx] = sv[h];
+                                if constexpr (SCH == SCHEME_EM_SUB) A.Tf[idx] = tv[h];
+                            }
+                        }
+                        v[m] = z;
+                        sE[0] += Ez.x;
+                        sE[1] += Ez.y;
+                        sJ[0] += Jz.x;
+                        sJ[1] += Jz.y;
+                        sE2 += Ez.x * Ez.x + Ez.y * Ez.y;
+                        if (outm) {
+                            A.Eout[idx] = mkc(Ez.x, (T)0);
+                            A.Eout[A.Ntot + idx] = mkc(Ez.y, (T)0);
+                        }
+                    }
+                }
+            };
+            switch (A.k.scheme) {
+                case SCHEME_MS: points(IntTag<SCHEME_MS>{}); break;
+                case SCHEME_EM: points(IntTag<SCHEME_EM>{}); break;
+                case SCHEME_MS_SUB: points(IntTag<SCHEME_MS_SUB>{}); break;
+                default: points(IntTag<SCHEME_EM_SUB>{}); break;
+            }
+            kahan_add(0, sE[0]);   // (the imaginary parts, slots 1, 3, 5, 7, stay zero)
+            kahan_add(2, sJ[0]);
+            kahan_add(4, sE[1]);
+            kahan_add(6, sJ[1]);
+            kahan_add(4 * D, sE2);
+        }
+        if (mode == MODE_ROW_OUTPUT) return;
+        LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+        __syncthreads();   // the transform's last reads of the exchange line are done
+#pragma unroll
+        for (int m = 0; m < E; ++m) Xb[pad16(t + TL * m)] = v[m];
+        __syncthreads();
+        if (active) {
+            C* Ho = A.X + row * HP;
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int k = t + TL * m;
+                if (k <= N / 2) {
+                    const C z = v[m], zp = Xb[pad16((N - k) & (N - 1))];
+                    Ho[k] = mkc((T)0.5 * (z.x + zp.x), (T)0.5 * (z.y - zp.y));
+                    Ho[A.Nh + k] = mkc((T)0.5 * (z.y + zp.y), (T)0.5 * (zp.x - z.x));
+                }
+            }
+        }
+    };
+
     int64_t item = blockIdx.x;
     if (item < n_items)
         for (int l = 0; l < L; ++l) prefetch_line(item, l);
@@ -482,57 +614,24 @@ row_pass(const PassArgs<T> A) {
         const int64_t base = row * N;
         const int64_t next = item + A.grid_blocks;
         const bool has_next = next < n_items;
+        if constexpr (D == 2) {
+            if (A.packed) {
+                packed_item(row, active, base, next, has_next);
+                continue;
+            }
+        }
 
         // 1. inverse x-DFT of every line, parked at this thread's own positions
-        if (A.packed) {
-            // Z = E_x + i E_y from the half spectra: Z(k) = X(k) + i Y(k) for
-            // k <= n/2 and conj(X(n-k)) + i conj(Y(n-k)) above (X, Y are the
-            // spectra of real rows); the first pass starts from Q = iq e instead
-            cp_async_wait_all();
+        for (int l = 0; l < L; ++l) {
+            cp_async_wait_pending(L - 1 - l);
             __syncthreads();
+            C* Sl = Sb + (l * LPB + g) * PS;
             C v[E];
-            if (mode == MODE_ROW_FIRST) {
 #pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const int pos = t + TL * m;
-                    T q;
-                    if (A.sigma)
-                        q = A.k.scheme == SCHEME_EM ? A.sigma[base + pos].x + A.k.s0.x : (T)1;
-                    else
-                        q = Mb[g * N + pos] ? A.k.iq_in.x : A.k.iq_out.x;
-                    v[m] = mkc(q * A.k.e[0], q * A.k.e[1]);
-                }
-            } else {
-                const C* Hx = Sb + g * PS;
-                const C* Hy = Sb + (LPB + g) * PS;
-#pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const int k = t + TL * m;
-                    if (k <= N / 2) {
-                        const C x = Hx[k], y = Hy[k];
-                        v[m] = mkc(x.x - y.y, x.y + y.x);
-                    } else {
-                        const C x = Hx[N - k], y = Hy[N - k];
-                        v[m] = mkc(x.x + y.y, y.x - x.y);
-                    }
-                }
-                LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
-            }
-            C* Sl = Sb + g * PS;
+            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
+            if (mode != MODE_ROW_FIRST) LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
 #pragma unroll
             for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
-        } else {
-            for (int l = 0; l < L; ++l) {
-                cp_async_wait_pending(L - 1 - l);
-                __syncthreads();
-                C* Sl = Sb + (l * LPB + g) * PS;
-                C v[E];
-#pragma unroll
-                for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
-                if (mode != MODE_ROW_FIRST) LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
-#pragma unroll
-                for (int m = 0; m < E; ++m) Sl[t + TL * m] = v[m];
-            }
         }
 
         // 2. pointwise scheme update and volume averages on real-space values,
@@ -546,80 +645,28 @@ row_pass(const PassArgs<T> A) {
             auto points = [&](auto tag) {
                 constexpr int SCH = decltype(tag)::value;
                 constexpr bool SUB = SCH == SCHEME_MS_SUB || SCH == SCHEME_EM_SUB;
-                if (A.packed) {
-                    // in batches of HB points: phase flags, and S (T) of the phase-1
-                    // points, first, so that their global loads are in flight
-                    // together before the first use
-                    constexpr int HB = (sizeof(T) == 4 ? 8 : 1) < E ? (sizeof(T) == 4 ? 8 : 1) : E;
-                    constexpr int UNR = sizeof(T) == 4 ? E / HB : 4;   // FP64: registers are scarcer
-#pragma unroll UNR
-                    for (int m0 = 0; m0 < E; m0 += HB) {
-                        bool inc[HB];
-                        C sv[HB], tv[HB];
-#pragma unroll
-                        for (int h = 0; h < HB; ++h) {
-                            const int pos = t + TL * (m0 + h);
-                            inc[h] = Mb[g * N + pos] != 0;
-                            sv[h] = tv[h] = mkc((T)0, (T)0);
-                            if constexpr (SUB) {
-                                if (inc[h]) sv[h] = A.S[base + pos];
-                            }
-                            if constexpr (SCH == SCHEME_EM_SUB) {
-                                if (inc[h]) tv[h] = A.Tf[base + pos];
-                            }
-                        }
-#pragma unroll
-                        for (int h = 0; h < HB; ++h) {
-                            const int pos = t + TL * (m0 + h);
-                            const int64_t idx = base + pos;
-                            C* zp = Sb + g * PS + pos;
-                            C z = *zp, Ez, Jz;
-                            if (!SUB && A.sigma)
-                                pointwise_field_packed<T>(A.k, z, A.sigma[idx].x, Ez, Jz);
-                            else
-                                pointwise_packed<T, SCH>(A.k, z, inc[h], sv[h], tv[h], Ez, Jz);
-                            if constexpr (SUB) {
-                                if (inc[h] && wst) {
-                                    A.S[idx] = sv[h];
-                                    if constexpr (SCH == SCHEME_EM_SUB) A.Tf[idx] = tv[h];
-                                }
-                            }
-                            *zp = z;
-                            sE[0][0] += Ez.x;
-                            sE[1][0] += Ez.y;
-                            sJ[0][0] += Jz.x;
-                            sJ[1][0] += Jz.y;
-                            sE2 += Ez.x * Ez.x + Ez.y * Ez.y;
-                            if (outm) {
-                                A.Eout[idx] = mkc(Ez.x, (T)0);
-                                A.Eout[A.Ntot + idx] = mkc(Ez.y, (T)0);
-                            }
-                        }
-                    }
-                } else {
 #pragma unroll 4
-                    for (int m = 0; m < E; ++m) {
-                        const int pos = t + TL * m;
-                        const int64_t idx = base + pos;
-                        const bool inc = Mb[g * N + pos] != 0;
-                        C q[D], Ev[D], Jv[D];
+                for (int m = 0; m < E; ++m) {
+                    const int pos = t + TL * m;
+                    const int64_t idx = base + pos;
+                    const bool inc = Mb[g * N + pos] != 0;
+                    C q[D], Ev[D], Jv[D];
 #pragma unroll
-                        for (int c = 0; c < D; ++c) q[c] = Sb[(c * LPB + g) * PS + pos];
-                        if (!SUB && A.sigma)
-                            pointwise_field<T, D>(A.k, q, A.sigma[idx], Ev, Jv);
-                        else
-                            pointwise<T, D, SCH>(A.k, q, inc, A.S ? A.S + idx : nullptr,
-                                                 A.Tf ? A.Tf + idx : nullptr, A.Ntot, Ev, Jv, wst);
+                    for (int c = 0; c < D; ++c) q[c] = Sb[(c * LPB + g) * PS + pos];
+                    if (!SUB && A.sigma)
+                        pointwise_field<T, D>(A.k, q, A.sigma[idx], Ev, Jv);
+                    else
+                        pointwise<T, D, SCH>(A.k, q, inc, A.S ? A.S + idx : nullptr,
+                                             A.Tf ? A.Tf + idx : nullptr, A.Ntot, Ev, Jv, wst);
 #pragma unroll
-                        for (int c = 0; c < D; ++c) {
-                            Sb[(c * LPB + g) * PS + pos] = q[c];
-                            sE[c][0] += Ev[c].x;
-                            sE[c][1] += Ev[c].y;
-                            sJ[c][0] += Jv[c].x;
-                            sJ[c][1] += Jv[c].y;
-                            sE2 += Ev[c].x * Ev[c].x + Ev[c].y * Ev[c].y;
-                            if (outm) A.Eout[c * A.Ntot + idx] = Ev[c];
-                        }
+                    for (int c = 0; c < D; ++c) {
+                        Sb[(c * LPB + g) * PS + pos] = q[c];
+                        sE[c][0] += Ev[c].x;
+                        sE[c][1] += Ev[c].y;
+                        sJ[c][0] += Jv[c].x;
+                        sJ[c][1] += Jv[c].y;
+                        sE2 += Ev[c].x * Ev[c].x + Ev[c].y * Ev[c].y;
+                        if (outm) A.Eout[c * A.Ntot + idx] = Ev[c];
                     }
                 }
             };
@@ -642,35 +689,7 @@ row_pass(const PassArgs<T> A) {
 
         // 3. forward x-DFT and store; the next item's line l is staged as soon as
         //    every thread has read line l of this item
-        if (mode != MODE_ROW_OUTPUT && A.packed) {
-            // forward DFT of Z, then the half spectra X = (Z(k) + conj Z(n-k))/2,
-            // Y = (Z(k) - conj Z(n-k))/(2i) for k = 0..n/2 (the partner values
-            // come through the exchange buffer)
-            C* Sl = Sb + g * PS;
-            C v[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = Sl[t + TL * m];
-            __syncthreads();
-            if (has_next)
-                for (int l = 0; l < L; ++l) prefetch_line(next, l);
-            LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
-            __syncthreads();
-#pragma unroll
-            for (int m = 0; m < E; ++m) Xb[pad16(t + TL * m)] = v[m];
-            __syncthreads();
-            if (active) {
-                C* Ho = A.X + row * HP;
-#pragma unroll
-                for (int m = 0; m < E; ++m) {
-                    const int k = t + TL * m;
-                    if (k <= N / 2) {
-                        const C z = v[m], zp = Xb[pad16((N - k) & (N - 1))];
-                        Ho[k] = mkc((T)0.5 * (z.x + zp.x), (T)0.5 * (z.y - zp.y));
-                        Ho[A.Nh + k] = mkc((T)0.5 * (z.y + zp.y), (T)0.5 * (zp.x - z.x));
-                    }
-                }
-            }
-        } else if (mode != MODE_ROW_OUTPUT) {
+        if (mode != MODE_ROW_OUTPUT) {
             for (int l = 0; l < L; ++l) {
                 C* Sl = Sb + (l * LPB + g) * PS;
                 C v[E];
