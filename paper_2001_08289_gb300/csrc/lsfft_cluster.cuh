@@ -1,7 +1,7 @@
 // Strided (y) pass for long 2-D columns on a thread-block cluster, with its
 // tiles moved by the tensor memory accelerator (TMA).
 //
-// One SM cannot stage enough adjacent columns of length N >= 2048, so a
+// One SM cannot stage enough adjacent columns of length N >= 4096, so a
 // cluster of CL blocks shares the work of an item of W adjacent columns
 // (16-byte row segments for CL = 2: W = 2 in FP32, 1 in FP64; 32-byte ones
 // for CL = 4).  With rows r = q + CL j (block rank q, j < M = N/CL) the length-N DFT
@@ -48,7 +48,7 @@ struct CluCfg {
     static constexpr int LINES = LS * W;
     static constexpr int E = sizeof(T) == 4 ? 16 : 8;
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
-    static constexpr int TL = M >= E ? M / E : 1;      // threads per line (only N >= 2048 is launched)
+    static constexpr int TL = M >= E ? M / E : 1;      // threads per line (only N >= 4096 is launched)
     static constexpr int COMPUTE = cmin(512, LINES * TL);   // threads that transform and exchange
     static constexpr int THREADS = COMPUTE + 32;       // + one producer warp for the TMA traffic
     static constexpr int G = COMPUTE / TL;             // lines transformed concurrently
@@ -63,7 +63,9 @@ struct CluCfg {
     static constexpr int Y_BYTES = LS * SLOT_BYTES;
     static constexpr int SLOT_WARPS = W * TL / 32;     // warps that transform one slot
     static constexpr int SMEM = Y_BYTES + G * XP * CS + 64;   // + four mbarriers
-    static constexpr bool SUPPORTED = N >= 2048 && SMEM <= 227 * 1024 && SPR >= 1 && G == SPR * W &&
+    // 2048-point columns fit the plain strided pass (two 16-byte columns per item),
+    // measured 30 % faster there than on clusters; the cluster pass takes 4096 and 8192
+    static constexpr bool SUPPORTED = N >= 4096 && SMEM <= 227 * 1024 && SPR >= 1 && G == SPR * W &&
                                       LS % SPR == 0 && M % BJ == 0 && COMPUTE == G * TL &&
                                       (W * TL) % 32 == 0;
 };

@@ -25,8 +25,8 @@ def L():
     return lib
 
 
-# (2048, 16): 2048-point columns on the cluster pass; (64, 64): the plain strided pass
-@pytest.mark.parametrize("shape", [(2048, 16), (64, 64)])
+# (4096, 16): 4096-point columns on the cluster pass; (64, 64): the plain strided pass
+@pytest.mark.parametrize("shape", [(4096, 16), (64, 64)])
 def test_bounded_tma_wait_reports_fault_and_recovers(L, shape):
     mask = random_mask(shape, 0.3, seed=3)
     e = [1.0, 0.0]
