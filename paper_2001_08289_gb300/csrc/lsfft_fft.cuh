@@ -182,7 +182,9 @@ __device__ __forceinline__ void line_sync() {
     else asm volatile("bar.sync 1, %0;" ::"n"(SYNC) : "memory");
 }
 
-template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false, int SYNC = 0>
+// SMS: element stride of the exchange line in shared memory (SMS lines
+// interleaved position by position share one buffer).
+template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false, int SYNC = 0, int SMS = 1>
 struct LineFFT {
     using C = cx<T>;
     static constexpr int TL = N / E;   // threads per line
@@ -268,13 +270,13 @@ struct LineFFT {
             } else {
                 const int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-                for (int r = 0; r < R; ++r) sm[pad16(base + r * NS)] = a[r];
+                for (int r = 0; r < R; ++r) sm[pad16(base + r * NS) * SMS] = a[r];
             }
         }
         if constexpr (!LAST) {
             line_sync<SYNC>();
 #pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m)];
+            for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m) * SMS];
             stage<NS * R>(v, sm, t, tw, tws);
         }
     }
