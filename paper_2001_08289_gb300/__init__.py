@@ -341,6 +341,19 @@ class Result:
         """Copy E into device memory at dst_ptr (e.g. a torch tensor's data_ptr())."""
         lsfft_copy_field(self._ptr, dst_ptr, True)
 
+    def field_tensor(self):
+        """E as a CUDA torch tensor of shape (d, *reversed(n)) that shares the
+        result's device memory (no copy).  The tensor keeps this Result alive;
+        the memory is released when both are gone."""
+        import torch
+
+        if self._ptr is None:
+            raise ValueError("the result has been freed")
+        dt = "<c8" if self.precision == FP32 else "<c16"
+        shape = (self.d,) + tuple(reversed(self.n))
+        holder = _DeviceArray(self, int(self._ptr.contents.E_device), shape, dt)
+        return torch.as_tensor(holder, device="cuda")
+
     def free(self):
         if self._ptr is not None:
             lsfft_free_result(self._ptr)
@@ -351,6 +364,15 @@ class Result:
             self.free()
         except Exception:
             pass
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ view of a result's device field; holds the Result."""
+
+    def __init__(self, owner, ptr: int, shape, typestr: str):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
 
 
 def make_opts(scheme="ms", precision="fp32", green="trig", tol=1e-6, max_iter=1000, stop_consecutive=3,

@@ -72,7 +72,9 @@ struct RowCfg {
     static constexpr int E = sizeof(T) == 4 ? (N < 16 ? N : 16) : (N < 8 ? N : 8);
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
     static constexpr int TL = N / E;
-    static constexpr int LPB = cmax(1, 256 / TL);                 // rows per item
+    // rows per item: fewer for 3 components, whose staging would otherwise
+    // leave room for one block per SM (measured ~20 % faster at 256^3 and 512^3)
+    static constexpr int LPB = cmax(1, (D == 3 ? 128 : 256) / TL);
     static constexpr int THREADS = LPB * TL;
     using P = Pitch<T, N, TL>;
     static constexpr int S_BYTES = D * LPB * P::S * CS;

@@ -220,3 +220,25 @@ def test_packed_real_layout_used_and_agrees_with_complex_layout(L, prec):
             assert np.linalg.norm(Ep - Ec) / np.linalg.norm(Ec) < (1e-12 if prec == "fp64" else 1e-5)
     with L.Grid(square_array_mask(16, d=3)) as g:
         assert not g.solve(5.0, [1.0, 0.0, 0.0], max_iter=3, tol=0.0).packed
+
+
+def test_field_tensor_is_a_zero_copy_view(L):
+    """Result.field_tensor() wraps the result's device field without copying and
+    keeps the result alive while the tensor is."""
+    import gc
+
+    import torch
+
+    mask = square_array_mask(32)
+    with L.Grid(mask) as g:
+        r = g.solve(10.0, [1.0, 0.0], scheme="ms", precision="fp32", tol=0.0, max_iter=3)
+        E = r.field_numpy()
+        ptr = int(r._ptr.contents.E_device)
+        t = r.field_tensor()
+        assert t.is_cuda and t.dtype == torch.complex64 and tuple(t.shape) == E.shape
+        assert t.data_ptr() == ptr
+        del r
+        gc.collect()
+        np.testing.assert_array_equal(t.cpu().numpy(), E)
+        del t
+        gc.collect()
