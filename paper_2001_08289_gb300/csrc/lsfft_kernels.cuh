@@ -840,11 +840,12 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
             __syncthreads();
             const int64_t inner0 = (item % cblocks) * COLS;
             const bool two_d = A.line_axis == 1;   // 2-D: inner = kx, line = ky; 3-D z: inner = kx + nx ky
+            // the COLS line starts of an item share ky (COLS divides nx): one division per item
+            const int kx0 = two_d ? (int)inner0 : (int)(inner0 % nx);
+            const int ky0 = two_d ? 0 : (int)(inner0 / nx);
             for (int p = threadIdx.x; p < N * COLS; p += Cfg::THREADS) {
                 const int kl = p / COLS, wc = p % COLS;
-                const int64_t inner = inner0 + wc;
-                const int kx = two_d ? (int)inner : (int)(inner % nx);
-                const int ki[3] = {kx, two_d ? kl : (int)(inner / nx), two_d ? 0 : kl};
+                const int ki[3] = {kx0 + wc, two_d ? kl : ky0, two_d ? 0 : kl};
                 C q[D];
 #pragma unroll
                 for (int cc = 0; cc < D; ++cc) q[cc] = Bi[(cc * N + kl) * COLS + wc];
