@@ -480,6 +480,22 @@ row_pass(const PassArgs<T> A) {
     // above) through the inverse DFT, the scheme update and the forward DFT to
     // their split (X = (Z(k) + conj Z(n-k))/2, Y = (Z(k) - conj Z(n-k))/(2i)), and
     // the next item is staged as soon as the join has read this one.
+    // Substituted schemes in the packed layout: bring the S (and T) rows of item
+    // `nxt` into L2 while the current item works, so that the scheme update finds
+    // them there (measured 5 % faster at 8192^2; with the three planes of the
+    // complex layout the extra requests cost more than they save).
+    auto prefetch_st = [&](int64_t nxt) {
+        if (!A.S) return;
+        constexpr int LINES128 = LPB * N * (int)sizeof(C) / 128;
+        const int64_t first = nxt * LPB * N;
+        const int64_t rows_left = A.n_lines - nxt * LPB;
+        const int lines = rows_left >= LPB ? LINES128 : (int)(rows_left * N * (int64_t)sizeof(C) / 128);
+        for (int i = threadIdx.x; i < lines; i += Cfg::THREADS) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(A.S + first) + 128 * i));
+            if (A.Tf)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(A.Tf + first) + 128 * i));
+        }
+    };
     auto packed_item = [&](int64_t row, bool active, int64_t base, int64_t next, bool has_next) {
         cp_async_wait_all();
         __syncthreads();
@@ -517,8 +533,10 @@ row_pass(const PassArgs<T> A) {
             if constexpr (N <= Cfg::RMAX) __syncthreads();   // (a one-stage transform has no barrier)
         }
         // every thread has read the staging buffers: stage the next item
-        if (has_next)
+        if (has_next) {
             for (int l = 0; l < 2; ++l) prefetch_line(next, l);
+            prefetch_st(next);
+        }
 
         if (active) {
             T sE[2] = {0, 0}, sJ[2] = {0, 0}, sE2 = 0;
