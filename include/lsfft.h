@@ -98,7 +98,8 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this solve launched (no-op launches included)     */
     int packed;                /* 1 if the packed real layout was used: 2-D with every scheme
                                   coefficient real (real sigma_1, real reference medium); the
-                                  two real components then share one complex plane         */
+                                  state then holds the x-spectra of the two real components
+                                  as two half-spectrum planes (E_device is complex as always) */
     int precision;             /* precision of E_device                                     */
     int d;
     int64_t n[3];

@@ -41,7 +41,7 @@ cudaError_t row_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
 template <typename T, int N, int D>
 cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
     if constexpr (D == 2 && CluCfg<T, N>::SUPPORTED) {
-        // long 2-D columns: cluster kernel (item = W adjacent columns or column pairs)
+        // long 2-D columns (4096, 8192): cluster kernel (item = W adjacent columns, both planes)
         using Cfg = CluCfg<T, N>;
         static int max_clusters = 0;
         if (op == OP_QUERY) {

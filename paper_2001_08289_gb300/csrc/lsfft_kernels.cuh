@@ -9,9 +9,11 @@
 //
 // Packed real layout (2-D, every scheme coefficient real, i.e. real sigma_1 and
 // a real reference medium): the fields are real (S and T purely imaginary), so
-// the two components travel as one complex plane Z = F_x + i F_y (S and T as
-// s_x + i s_y with S = i s), halving bytes and transforms.  The strided pass
-// then splits the spectra with the Hermitian pairing of k and -k.
+// the row pass transforms the two components as one complex line
+// Z = F_x + i F_y (S and T as s_x + i s_y with S = i s) and keeps the x-spectra
+// of F_x and F_y as two half-spectrum planes (k_x = 0..n_x/2, padded pitch):
+// half the bytes and transforms of the complex layout, and the strided pass
+// sees ordinary columns.
 //
 // One iteration (2-D): row pass [inverse x-DFT -> pointwise scheme update and
 // volume averages -> forward x-DFT], finalize (FP64 sums, sigma_k, stop rule),
@@ -20,13 +22,10 @@
 // y inverse.  Every pass is in place.
 //
 // Both passes are persistent: a block owns a stream of work items (a few rows,
-// or a few line starts of the strided axis).  The lines of an item are staged
-// in shared memory by cp.async, one commit group per line; a thread transforms
-// one line at a time in registers (positions t + TL*m) and parks the result
-// back in the stage buffer at its own positions, so the pointwise update and
-// the Gamma multiply read all lines without extra barriers.  As soon as the
-// last pass over a staged line has read it, the copy of the next item's line
-// is issued, so loads overlap the remaining transforms of the current item.
+// or a few line starts of the strided axis).  Row items are staged in shared
+// memory by cp.async (contiguous rows), strided items by one TMA box; a thread
+// transforms one line at a time in registers (positions t + TL*m), and the next
+// item is staged as soon as the current one has been read.
 #pragma once
 
 #include <cuda.h>   // CUtensorMap (the encoding itself goes through the runtime's driver entry point)
