@@ -309,3 +309,34 @@ def test_insulating_squares_experiment():
         assert abs(r.sigma_star - s) < 1e-9
     assert out["em_sub"].iterations < out["ms"].iterations
     assert abs(s - np.sqrt(1.0 / 3.0)) < 1e-3
+
+
+def test_estimate_sensitivity_of_the_slit():
+    """Section "Estimating the parameters alpha and beta": a slit estimate wider
+    than the exact weighted-pole interval still converges, at the slower rate its
+    own t predicts (Eq. J46); one that leaves poles outside still converges, but
+    the poles outside set a factor above the nominal |z| of the estimate."""
+    mask = square_array_mask(32)
+    e = np.array([1.0, 0.0])
+    m, w = X.poles(mask, e, "fd")
+    a, b, _, _ = X.pole_hull(m, w, cutoff=1e-10)
+    s1 = 100.0
+    ref = None
+    runs = {}
+    for name, (aa, bb) in {"exact": (a, b), "wide": (a * 0.8, b * 1.25), "narrow": (a * 1.4, b * 0.7)}.items():
+        r = S.solve(S.Problem(mask, s1, e, "fd"), "em_sub", alpha=aa, beta=bb, tol=1e-12, max_iter=3000)
+        assert r.status == S.STATUS_OK
+        ref = r.sigma_star if ref is None else ref
+        assert abs(r.sigma_star - ref) < 1e-9
+        err = np.abs(r.hist_sigma - r.sigma_star)
+        # observed asymptotic factor over a window where the error is well above rounding
+        ok = np.nonzero(err > 1e-11)[0]
+        k1 = ok[-1]
+        k0 = max(1, k1 - 8)
+        observed = (err[k1] / err[k0]) ** (1.0 / (k1 - k0))
+        runs[name] = (r.iterations, observed, S.predicted_rate("em_sub", s1, aa, bb))
+    assert runs["wide"][0] >= runs["exact"][0] and runs["narrow"][0] >= runs["exact"][0]
+    assert runs["wide"][2] > runs["exact"][2]
+    assert runs["exact"][1] <= runs["exact"][2] * 1.05
+    assert runs["wide"][1] <= runs["wide"][2] * 1.05
+    assert runs["narrow"][1] > runs["narrow"][2] * 1.05
