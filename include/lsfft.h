@@ -147,6 +147,17 @@ int lsfft_solve(lsfft_grid *grid, lsfft_c128 sigma1, const double *e,
  * device pointer.  Synchronises the grid's stream. */
 int lsfft_copy_field(const lsfft_result *res, void *dst, int dst_on_device);
 
+/* Stream-ordered form of lsfft_copy_field: enqueue the copy of E on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream) and return
+ * without waiting, so that the copy of one solve's field overlaps the next
+ * solve on the grid's stream.  E is complete when lsfft_solve returns, so no
+ * ordering against the grid's stream is needed.  The caller keeps `res` and
+ * `dst` alive until the copy has completed on that stream (synchronise it, or
+ * an event recorded after this call); a pageable host `dst` makes the copy
+ * synchronous, pinned host memory lets it run on a copy engine.  EINVAL for a
+ * null result, destination or field; ECUDA if the copy cannot be enqueued. */
+int lsfft_copy_field_async(const lsfft_result *res, void *dst, int dst_on_device, void *cuda_stream);
+
 /* Free the result's host history and device field. */
 void lsfft_free_result(lsfft_result *res);
 

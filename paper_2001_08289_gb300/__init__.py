@@ -25,7 +25,8 @@ __all__ = [
     "OK", "EINVAL", "ENOMEM", "ENOTCONV", "EDIVERGED", "ECUDA",
     "LsfftError", "Opts", "Result", "Grid", "load_library", "library_path",
     "lsfft_version", "lsfft_last_error", "lsfft_strerror", "lsfft_create_grid", "lsfft_create_grid_device",
-    "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_free_result",
+    "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_copy_field_async",
+    "lsfft_free_result",
     "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
     "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "lsfft_solve_batch", "solve_batch",
     "lsfft_substitution_rates", "lsfft_debug_inject",
@@ -105,6 +106,7 @@ def load_library():
     lib.lsfft_solve.argtypes = [C.c_void_p, _C128, C.POINTER(C.c_double), C.POINTER(Opts),
                                 C.POINTER(C.POINTER(_Result))]
     lib.lsfft_copy_field.argtypes = [C.POINTER(_Result), C.c_void_p, C.c_int]
+    lib.lsfft_copy_field_async.argtypes = [C.POINTER(_Result), C.c_void_p, C.c_int, C.c_void_p]
     lib.lsfft_free_result.argtypes = [C.POINTER(_Result)]
     lib.lsfft_free_result.restype = None
     lib.lsfft_prepare.argtypes = [C.c_void_p, _C128, C.POINTER(C.c_double), C.POINTER(Opts)]
@@ -192,6 +194,12 @@ def lsfft_solve(grid: int, sigma1: complex, e, opts: Opts):
 
 def lsfft_copy_field(res, dst_ptr: int, dst_on_device: bool) -> None:
     _check(load_library().lsfft_copy_field(res, C.c_void_p(dst_ptr), int(bool(dst_on_device))))
+
+
+def lsfft_copy_field_async(res, dst_ptr: int, dst_on_device: bool, stream: int = 0) -> None:
+    """Enqueue the copy of E on `stream` (a cudaStream_t as int) and return at once."""
+    _check(load_library().lsfft_copy_field_async(res, C.c_void_p(dst_ptr), int(bool(dst_on_device)),
+                                                 C.c_void_p(stream)))
 
 
 def lsfft_free_result(res) -> None:
@@ -340,6 +348,14 @@ class Result:
     def field_into(self, dst_ptr: int) -> None:
         """Copy E into device memory at dst_ptr (e.g. a torch tensor's data_ptr())."""
         lsfft_copy_field(self._ptr, dst_ptr, True)
+
+    def field_into_async(self, dst_ptr: int, on_device: bool, stream: int) -> None:
+        """Enqueue the copy of E to dst_ptr (pinned host or device memory) on
+        `stream` and return; keep this Result and the destination alive until
+        the stream has run the copy."""
+        if self._ptr is None:
+            raise ValueError("the result has been freed")
+        lsfft_copy_field_async(self._ptr, dst_ptr, on_device, stream)
 
     def field_tensor(self):
         """E as a CUDA torch tensor of shape (d, *reversed(n)) that shares the

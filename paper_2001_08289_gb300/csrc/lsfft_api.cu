@@ -87,6 +87,7 @@ struct lsfft_grid {
     SchemeParams* prm_host = nullptr;   // constants of the current solve (kernel parameters)
     Ctrl* ctrl_dev = nullptr;
     Ctrl* ctrl_host = nullptr;          // pinned
+    Ctrl* ctrl_host_dev = nullptr;      // its device view (written by a small kernel)
     void* tw[3] = {nullptr, nullptr, nullptr};   // FP64 twiddles W_n^k per axis
     void* fd[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // FD symbol per axis, FP32/FP64
     bool prepared[2] = {false, false};
@@ -100,6 +101,7 @@ struct lsfft_grid {
     void* cur_E = nullptr;
     lsfft_result* cur_res = nullptr;
     double* hist_host = nullptr;    // pinned copy of the history
+    double* hist_host_dev = nullptr;   // its device view
     int hist_host_cap = 0;
     cudaEvent_t ev_check = nullptr;
     // per-voxel conductivity mode (lsfft_set_sigma_field)
@@ -298,6 +300,7 @@ int create_common(int d, const int64_t n[3], const uint8_t* mask, bool on_device
     }
     if (e == cudaSuccess) e = cudaMalloc(&g->ctrl_dev, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost(&g->ctrl_host, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&g->ctrl_host_dev, g->ctrl_host, 0);
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_check, cudaEventDisableTiming);
@@ -770,6 +773,7 @@ int begin_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
         g->hist_host_cap = 0;
         CK(cudaMallocHost(&g->hist_host, sizeof(double) * HIST_STRIDE * g->hist_cap));
         g->hist_host_cap = g->hist_cap;
+        CK(cudaHostGetDevicePointer((void**)&g->hist_host_dev, g->hist_host, 0));
     }
     // Every finalize either sets `done` or advances the iteration count, so at
     // most max_iter / check_every + 1 graph launches are needed; the bound only
@@ -777,13 +781,13 @@ int begin_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     g->cur_max_launches = (int64_t)o->max_iter / o->check_every + 2;
     g->cur_launches = 0;
     g->cur_per_iter = g->d == 2 ? 3 : 5;      // row pass, finalize, strided pass(es)
-    g->cur_kernels = 1 + g->cur_per_iter;     // init + first update
+    g->cur_kernels = 2 + g->cur_per_iter;     // init + first update + control block readback
     g->cur_check_every = o->check_every;
     g->cur_st = st;
     g->cur_nblocks = nblocks;
     g->cur_E = nullptr;
     g->cur_res = res;
-    CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+    CK(launch_copy_words(g->ctrl_host_dev, g->ctrl_dev, sizeof(Ctrl), g->stream));
     CK(cudaEventRecord(g->ev_check, g->stream));
     g->phase = 1;
     return LSFFT_OK;
@@ -841,17 +845,16 @@ int poll_solve(lsfft_grid* g) {
     }
     if (g->ctrl_host->done) {
         // output pass: E of the last iterate, its sigma_* and averages, history
-        g->cur_kernels += 2;
+        g->cur_kernels += 4;   // output row pass, finalize, two readbacks
         const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
         CK(cudaMallocAsync(&g->cur_E, ebytes, g->stream));
         CK(launch_row<T>(g, g->cur_st, MODE_ROW_OUTPUT, (cx<T>*)g->cur_E));
         CK(launch_finalize(g->partials, g->cur_nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1,
                            g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
-        CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+        CK(launch_copy_words(g->ctrl_host_dev, g->ctrl_dev, sizeof(Ctrl), g->stream));
         const int L = g->ctrl_host->iter + 1;
-        CK(cudaMemcpyAsync(g->hist_host, g->hist, sizeof(double) * HIST_STRIDE * L, cudaMemcpyDeviceToHost,
-                           g->stream));
+        CK(launch_copy_words(g->hist_host_dev, g->hist, sizeof(double) * HIST_STRIDE * L, g->stream));
         CK(cudaEventRecord(g->ev_check, g->stream));
         g->phase_finish = true;
         g->phase = 1;
@@ -862,8 +865,8 @@ int poll_solve(lsfft_grid* g) {
         return LSFFT_ECUDA;
     }
     CK(cudaGraphLaunch(g->cur_exec, g->stream));
-    g->cur_kernels += (int64_t)g->cur_per_iter * g->cur_check_every;
-    CK(cudaMemcpyAsync(g->ctrl_host, g->ctrl_dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+    g->cur_kernels += (int64_t)g->cur_per_iter * g->cur_check_every + 1;
+    CK(launch_copy_words(g->ctrl_host_dev, g->ctrl_dev, sizeof(Ctrl), g->stream));
     CK(cudaEventRecord(g->ev_check, g->stream));
     g->phase = 1;
     return 0;
@@ -1041,6 +1044,19 @@ int lsfft_copy_field(const lsfft_result* res, void* dst, int dst_on_device) {
     const size_t bytes = (size_t)res->d * N * (res->precision == LSFFT_FP32 ? 8 : 16);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(dst, res->E_device, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return LSFFT_OK;
+}
+
+int lsfft_copy_field_async(const lsfft_result* res, void* dst, int dst_on_device, void* cuda_stream) {
+    if (!res || !dst || !res->E_device) {
+        g_last_error = "null argument";
+        return LSFFT_EINVAL;
+    }
+    size_t N = 1;
+    for (int a = 0; a < res->d; ++a) N *= (size_t)res->n[a];
+    const size_t bytes = (size_t)res->d * N * (res->precision == LSFFT_FP32 ? 8 : 16);
+    CK(cudaMemcpyAsync(dst, res->E_device, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       (cudaStream_t)cuda_stream));
     return LSFFT_OK;
 }
 

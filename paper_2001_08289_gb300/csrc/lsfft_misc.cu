@@ -137,6 +137,22 @@ cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const S
     return cudaGetLastError();
 }
 
+// Small device-to-host transfers (the control block, the history) written by
+// one block into mapped pinned host memory: they do not queue on a copy engine
+// behind a large field copy running on another stream.
+__global__ void copy_words_kernel(unsigned long long* __restrict__ dst, const unsigned long long* __restrict__ src,
+                                  int64_t words) {
+    for (int64_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_copy_words(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes % 8 != 0) return cudaErrorInvalidValue;
+    if (bytes == 0) return cudaSuccess;
+    copy_words_kernel<<<1, 256, 0, s>>>((unsigned long long*)dst, (const unsigned long long*)src,
+                                        (int64_t)(bytes / 8));
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_init<float>(cx<float>*, cx<float>*, cx<float>*, const uint8_t*, const SchemeParams&,
                                         int64_t, int, int, const cx<float>*, int, cudaStream_t);
 template cudaError_t launch_init<double>(cx<double>*, cx<double>*, cx<double>*, const uint8_t*, const SchemeParams&,

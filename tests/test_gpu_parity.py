@@ -242,3 +242,30 @@ def test_field_tensor_is_a_zero_copy_view(L):
         np.testing.assert_array_equal(t.cpu().numpy(), E)
         del t
         gc.collect()
+
+
+def test_async_field_copy_matches_the_synchronous_copy(L):
+    """lsfft_copy_field_async delivers the same bytes as lsfft_copy_field, to
+    pinned host memory and to device memory, while another solve runs on the
+    grid's stream."""
+    import torch
+
+    mask = square_array_mask(64)
+    with L.Grid(mask) as g:
+        r1 = g.solve(10.0, [1.0, 0.0], scheme="ms", precision="fp32", tol=0.0, max_iter=5)
+        E1 = r1.field_numpy()
+        host = torch.empty(E1.shape, dtype=torch.complex64).pin_memory()
+        dev = torch.empty(E1.shape, dtype=torch.complex64, device="cuda")
+        cs = torch.cuda.Stream()
+        r1.field_into_async(host.data_ptr(), False, cs.cuda_stream)
+        r1.field_into_async(dev.data_ptr(), True, cs.cuda_stream)
+        r2 = g.solve(0.1, [0.0, 1.0], scheme="em_sub", precision="fp32", tol=0.0, max_iter=5,
+                     alpha=0.25, beta=4.0)
+        cs.synchronize()
+        np.testing.assert_array_equal(host.numpy(), E1)
+        np.testing.assert_array_equal(dev.cpu().numpy(), E1)
+        assert not np.array_equal(r2.field_numpy(), E1)
+        r1.free()
+        r2.free()
+        with pytest.raises(ValueError):
+            r1.field_into_async(host.data_ptr(), False, cs.cuda_stream)

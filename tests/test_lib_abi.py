@@ -81,3 +81,12 @@ def test_tridiag_gauss_matches_dense_eigh(lib):
 def test_debug_inject_rejects_null_grid_without_gpu(lib):
     lib.lsfft_debug_inject.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert lib.lsfft_debug_inject(None, 1) == 1
+
+
+def test_field_copies_reject_null_arguments_without_gpu(lib):
+    lib.lsfft_copy_field.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    lib.lsfft_copy_field_async.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    buf = ctypes.create_string_buffer(16)
+    assert lib.lsfft_copy_field(None, buf, 0) == 1
+    assert lib.lsfft_copy_field_async(None, buf, 0, None) == 1
+    assert lib.lsfft_copy_field_async(None, None, 1, None) == 1
