@@ -72,8 +72,10 @@ struct RowCfg {
     static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
     static constexpr int TL = N / E;
     // rows per item: small blocks, so that several fit an SM (measured 25 %
-    // faster than 256-thread items at 256^3 and 512^3, 14 % at 256^2)
-    static constexpr int LPB = cmax(1, (D == 3 ? 64 : 128) / TL);
+    // faster than 256-thread items at 256^3 and 512^3, 14 % at 256^2).  FP64
+    // 2-D rows are bound by the FP64 pipe of each SM: one warp per item spreads
+    // the rows of a small grid over the most SMs.
+    static constexpr int LPB = sizeof(T) == 8 && D == 2 ? cmax(1, 32 / TL) : cmax(1, (D == 3 ? 64 : 128) / TL);
     static constexpr int THREADS = LPB * TL;
     using P = Pitch<T, N, TL>;
     static constexpr int S_BYTES = D * LPB * P::S * CS;
@@ -98,8 +100,11 @@ struct ColCfg {
     static constexpr int xp() { return roundup16(N + N / 16) + 8; }
     static constexpr int bytes(int cols) { return 2 * item_bytes(cols) + D * cols * xp() * CS + 64; }
     // adjacent line starts per item: a 32-byte row segment, or 16 bytes when
-    // two item buffers of 32-byte segments do not fit
-    static constexpr int COLS = bytes(32 / CS) <= 220 * 1024 ? 32 / CS : 16 / CS;
+    // two item buffers of 32-byte segments do not fit.  FP64 2-D columns take
+    // one line start per item (16 bytes): the FP64 pipe, not DRAM, bounds them,
+    // and small grids then spread over twice as many SMs.
+    static constexpr int COLS = sizeof(T) == 8 && D == 2 ? 16 / CS
+                                : bytes(32 / CS) <= 220 * 1024 ? 32 / CS : 16 / CS;
     static constexpr int THREADS = D * COLS * TL;                 // every line of an item at once
     static constexpr int ITEM_BYTES = item_bytes(COLS);
     static constexpr int XP = xp();

@@ -45,26 +45,39 @@ constexpr int FIN_THREADS = 256;
 __global__ void __launch_bounds__(FIN_THREADS)
 finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const SchemeParams P,
                 Ctrl* __restrict__ ctrl, double* __restrict__ hist, int final_mode) {
-    __shared__ double tot[16];
-    __shared__ double red[FIN_THREADS / 32];
+    constexpr int NVMAX = 16;   // nv = 4 d + 1 <= 13
+    __shared__ double tot[NVMAX];
+    __shared__ double red[FIN_THREADS / 32][NVMAX];
     if (!final_mode && ctrl->done) {
         if (threadIdx.x == 0) ctrl->skipB = 1;
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = 0; v < nv; ++v) {
-        double x = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += FIN_THREADS) x += partials[(int64_t)b * nv + v];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp] = x;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int w = 0; w < FIN_THREADS / 32; ++w) s += red[w];
-            tot[v] = s;
-        }
-        __syncthreads();
+    // every value at once (its loads in flight together), each in the same
+    // fixed order: blocks strided over the threads, a shuffle tree, the warps
+    double x[NVMAX];
+#pragma unroll
+    for (int v = 0; v < NVMAX; ++v) x[v] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += FIN_THREADS) {
+        const double* pb = partials + (int64_t)b * nv;
+#pragma unroll
+        for (int v = 0; v < NVMAX; ++v)
+            if (v < nv) x[v] += pb[v];
     }
+#pragma unroll
+    for (int v = 0; v < NVMAX; ++v) {
+        if (v < nv) {
+            for (int o = 16; o > 0; o >>= 1) x[v] += __shfl_down_sync(0xffffffffu, x[v], o);
+            if (lane == 0) red[warp][v] = x[v];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double s = 0.0;
+        for (int w = 0; w < FIN_THREADS / 32; ++w) s += red[w][threadIdx.x];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     const int d = P.d;
     // sigma_k = (<J>.e) / (<E>.e); the 1/N factors cancel
@@ -227,12 +240,13 @@ __global__ void vec_scale(cx<T>* __restrict__ dst, const cx<T>* __restrict__ src
         dst[i] = mkc((T)((double)src[i].x * s), (T)((double)src[i].y * s));
 }
 
+// One warp: lane l sums partials l, l + 32, ... in order, then a fixed shuffle
+// tree (deterministic; the loads of a lane are independent, so they overlap).
 __global__ void vec_sum_partials(const double* __restrict__ partials, int n, double* __restrict__ out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < n; ++b) s += partials[b];   // fixed order
-        out[0] = s;
-    }
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += 32) s += partials[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[0] = s;
 }
 
 template <typename T>
