@@ -73,9 +73,10 @@ struct RowCfg {
     static constexpr int TL = N / E;
     // rows per item: small blocks, so that several fit an SM (measured 25 %
     // faster than 256-thread items at 256^3 and 512^3, 14 % at 256^2).  FP64
-    // 2-D rows are bound by the FP64 pipe of each SM: one warp per item spreads
-    // the rows of a small grid over the most SMs.
-    static constexpr int LPB = sizeof(T) == 8 && D == 2 ? cmax(1, 32 / TL) : cmax(1, (D == 3 ? 64 : 128) / TL);
+    // 2-D rows are bound by the FP64 pipe, whose rate is per warp scheduler: one
+    // row per item puts each row of a small grid on a scheduler of its own (64^2
+    // lattice: 64 rows on 64 schedulers, where 16-row items used 16).
+    static constexpr int LPB = sizeof(T) == 8 && D == 2 ? 1 : cmax(1, (D == 3 ? 64 : 128) / TL);
     static constexpr int THREADS = LPB * TL;
     using P = Pitch<T, N, TL>;
     static constexpr int S_BYTES = D * LPB * P::S * CS;
@@ -139,9 +140,25 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
 // ---------------------------------------------------------------------------
 // Reductions: thread-local FP64 -> warp shuffle -> block -> partials[block][NV]
 // ---------------------------------------------------------------------------
-template <int NV>
+template <int NV, int NT>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], double* __restrict__ out) {
     __shared__ double red[32][NV];
+    if constexpr (NT < 32) {
+        // a block narrower than a warp (short FP64 rows): thread 0 adds the
+        // threads' sums in order
+#pragma unroll
+        for (int v = 0; v < NV; ++v) red[threadIdx.x][v] = acc[v];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double x = 0.0;
+                for (int i = 0; i < NT; ++i) x += red[i][v];
+                out[v] = x;
+            }
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -737,7 +754,7 @@ row_pass(const PassArgs<T> A) {
     double dacc[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) dacc[i] = (double)acc[i] - (double)cmp[i];
-    block_reduce_store<NV>(dacc, A.partials + (int64_t)blockIdx.x * NV);
+    block_reduce_store<NV, Cfg::THREADS>(dacc, A.partials + (int64_t)blockIdx.x * NV);
 }
 
 // ---------------------------------------------------------------------------
