@@ -368,6 +368,18 @@ def run_ours(args, sigmas):
         e2e_vox = 0
         copies = 0
         prev = None
+        # this box's device-to-host rate into pinned memory, for context (untimed)
+        probe = torch.empty((2, n, n), dtype=torch.complex64, device=dev)
+        with torch.cuda.stream(copy_stream):
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            host_E[0].copy_(probe, non_blocking=True)
+            c0.record(copy_stream)
+            host_E[0].copy_(probe, non_blocking=True)
+            c1.record(copy_stream)
+        copy_stream.synchronize()
+        d2h_gbps = probe.numel() * 8 / (c0.elapsed_time(c1) * 1e6)
+        del probe
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -392,6 +404,7 @@ def run_ours(args, sigmas):
         if prev is not None:
             L.lsfft_free_result(prev)
         e2e = {"value": e2e_vox / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "d2h_gbps_pinned": round(d2h_gbps, 1),
                "note": "lsfft_create_grid from pinned host mask, lsfft_solve per (sigma1, scheme), "
                        "lsfft_copy_field_async of every E to pinned host memory on a copy stream (overlapping "
                        "the next solve), host wall clock until the last copy has landed"}
