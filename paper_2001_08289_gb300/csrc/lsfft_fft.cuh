@@ -228,9 +228,15 @@ struct LineFFT {
         }
     }
 
+    // FP64 lines of two points per thread (radix 2 throughout): every stage's
+    // single twiddle is loaded up front, so that the table reads of the stages
+    // are in flight together instead of one cache latency per stage.
+    static constexpr bool PRE = sizeof(T) == 8 && E == 2 && RMAX == 2;
+    static constexpr int LOGN = ilog2c(N);
+
     template <int NS>
     __device__ __forceinline__ static void stage(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
-                                                 int tws) {
+                                                 int tws, const C* pre) {
         constexpr int REM = N / NS;
         constexpr int R = REM >= RMAX ? RMAX : REM;
         constexpr bool LAST = (NS * R == N);
@@ -260,6 +266,8 @@ struct LineFFT {
             if constexpr (SHARED_TW) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) a[r] = cmul(a[r], mul_root16<INV>(pw[r], (i * r * (16 / E)) & 15));
+            } else if constexpr (NS > 1 && PRE) {
+                a[1] = INV ? cmulc(a[1], pre[ilog2c(NS)]) : cmul(a[1], pre[ilog2c(NS)]);
             } else if constexpr (NS > 1) {
                 twiddle<R>(a, j % NS, NS * R, tw, tws);
             }
@@ -277,7 +285,7 @@ struct LineFFT {
             line_sync<SYNC>();
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m) * SMS];
-            stage<NS * R>(v, sm, t, tw, tws);
+            stage<NS * R>(v, sm, t, tw, tws, pre);
         }
     }
 
@@ -288,7 +296,13 @@ struct LineFFT {
     // decimated part of a longer one).
     __device__ __forceinline__ static void run(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
                                                int tws = 1) {
-        stage<1>(v, sm, t, tw, tws);
+        C pre[PRE ? LOGN : 1];
+        if constexpr (PRE) {
+            // stage NS = 2^s (s >= 1): W_{2 NS}^(t mod NS) = W_L^((N / (2 NS)) (t mod NS) tws)
+#pragma unroll
+            for (int s = 1; s < LOGN; ++s) pre[s] = tw[(int64_t)(N >> (s + 1)) * (t & ((1 << s) - 1)) * tws];
+        }
+        stage<1>(v, sm, t, tw, tws, pre);
     }
 };
 

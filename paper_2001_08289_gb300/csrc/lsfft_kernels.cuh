@@ -65,11 +65,23 @@ __host__ __device__ constexpr int min_blocks(int smem, int threads) {
 // move whole 32-byte row segments of any aligned group of adjacent columns.
 __host__ __device__ constexpr int64_t half_pitch(int64_t nx) { return nx / 2 + 4; }
 
+// Points per thread (E) and largest radix of a line transform.  FP64 2-D lines
+// of at most 64 points take two points per thread, so that one line fills a
+// warp: the FP64 pipe of this GPU gave a warp with 8 of 32 lanes active nearly
+// the time of a full one (64^2 rows: one row of 8 threads per warp instead of
+// four made the pass only 1.25x faster), so fewer instructions per thread win.
+template <typename T, int N, int D>
+struct LineShape {
+    static constexpr bool NARROW64 = sizeof(T) == 8 && D == 2 && N >= 4 && N <= 64;
+    static constexpr int E = NARROW64 ? 2 : sizeof(T) == 4 ? (N < 16 ? N : 16) : (N < 8 ? N : 8);
+    static constexpr int RMAX = NARROW64 ? 2 : sizeof(T) == 4 ? 16 : 8;
+};
+
 template <typename T, int N, int D>
 struct RowCfg {
     static constexpr int CS = (int)sizeof(cx<T>);
-    static constexpr int E = sizeof(T) == 4 ? (N < 16 ? N : 16) : (N < 8 ? N : 8);
-    static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int E = LineShape<T, N, D>::E;
+    static constexpr int RMAX = LineShape<T, N, D>::RMAX;
     static constexpr int TL = N / E;
     // rows per item: small blocks, so that several fit an SM (measured 25 %
     // faster than 256-thread items at 256^3 and 512^3, 14 % at 256^2).  FP64
@@ -93,8 +105,8 @@ struct RowCfg {
 template <typename T, int N, int D>
 struct ColCfg {
     static constexpr int CS = (int)sizeof(cx<T>);
-    static constexpr int E = sizeof(T) == 4 ? (N < 16 ? N : 16) : (N < 8 ? N : 8);
-    static constexpr int RMAX = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int E = LineShape<T, N, D>::E;
+    static constexpr int RMAX = LineShape<T, N, D>::RMAX;
     static constexpr int TL = N / E;
     static constexpr int EPC = CS / 8;                            // 8-byte tensor elements per value
     static constexpr int item_bytes(int cols) { return D * N * cols * CS; }
@@ -165,8 +177,13 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], double* __
         double x = acc[v];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp][v] = x;
+        if constexpr (NT == 32) {   // one warp: its sum is the block's
+            if (lane == 0) out[v] = x;
+        } else {
+            if (lane == 0) red[warp][v] = x;
+        }
     }
+    if constexpr (NT == 32) return;
     __syncthreads();
     if (warp == 0) {
         const int nw = (blockDim.x + 31) >> 5;
@@ -483,13 +500,17 @@ row_pass(const PassArgs<T> A) {
         cp_async_commit();
     };
 
-    // Running per-thread sums over items, compensated (Kahan) in the field
-    // precision: the FP64 pipe of the GPU is far slower than FP32, so in FP32
-    // mode doubles enter only in the block and grid reductions at the end.
+    // Running per-thread sums over items in the field precision, compensated
+    // (Kahan) in FP32: the FP64 pipe of the GPU is far slower than FP32, so in
+    // FP32 mode doubles enter only in the block and grid reductions at the end.
     T acc[NV], cmp[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = cmp[i] = (T)0;
     auto kahan_add = [&](int i, T x) {
+        if constexpr (sizeof(T) == 8) {   // FP64 needs no compensation (and its pipe is slow)
+            acc[i] += x;
+            return;
+        }
         const T y = x - cmp[i];
         const T tsum = acc[i] + y;
         cmp[i] = (tsum - acc[i]) - y;
