@@ -44,6 +44,59 @@ int fail_cuda(cudaError_t e, const char* what) {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// Stream-ordered memory pool (one per device) for the large buffers: grid
+// workspaces and result fields.  A freed block stays cached in the pool for the
+// next grid or solve instead of being unmapped and mapped again (a 1 GB field
+// cost about 1.4 ms per cudaFree from the default pool, which returns memory at
+// every synchronisation); the pool is trimmed once no such buffer is alive.
+struct BigPool {
+    std::mutex mu;
+    cudaMemPool_t pool[64] = {};
+    long live = 0;
+};
+BigPool& big_pool() {
+    static BigPool p;
+    return p;
+}
+
+cudaError_t big_alloc(void** ptr, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    BigPool& P = big_pool();
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (!P.pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        e = cudaMemPoolCreate(&P.pool[dev], &props);
+        if (e != cudaSuccess) {
+            P.pool[dev] = nullptr;
+            return e;
+        }
+        unsigned long long keep = ~0ull;
+        e = cudaMemPoolSetAttribute(P.pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMallocFromPoolAsync(ptr, bytes, P.pool[dev], s);
+    if (e == cudaSuccess) ++P.live;
+    return e;
+}
+
+// Release a big_alloc buffer (waits for the device, as cudaFree does); null is a no-op.
+void big_free(void* ptr) {
+    if (!ptr) return;
+    cudaFree(ptr);
+    BigPool& P = big_pool();
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (--P.live == 0)
+        for (int d = 0; d < 64; ++d)
+            if (P.pool[d]) cudaMemPoolTrimTo(P.pool[d], 0);
+}
+
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2i(int64_t v) {
     int r = 0;
@@ -179,15 +232,17 @@ int prepare_kernels(lsfft_grid* g) {
 int ensure_workspace(lsfft_grid* g, int prec, int st, int max_iter) {
     if (g->ws_prec != prec || g->ws_st < st) {
         clear_graphs(g);
-        cudaFree(g->X);
-        cudaFree(g->S);
-        cudaFree(g->T);
+        big_free(g->X);
+        big_free(g->S);
+        big_free(g->T);
         g->X = g->S = g->T = nullptr;
         g->ws_prec = -1;
         const size_t bytes = (size_t)g->d * g->N * (prec == LSFFT_FP32 ? 8 : 16);
-        if (cudaMalloc(&g->X, bytes) != cudaSuccess) return fail_cuda(cudaErrorMemoryAllocation, "workspace X");
-        if (st >= 1 && cudaMalloc(&g->S, bytes) != cudaSuccess) return fail_cuda(cudaErrorMemoryAllocation, "workspace S");
-        if (st >= 2 && cudaMalloc(&g->T, bytes) != cudaSuccess) return fail_cuda(cudaErrorMemoryAllocation, "workspace T");
+        if (big_alloc(&g->X, bytes, g->stream) != cudaSuccess) return fail_cuda(cudaErrorMemoryAllocation, "workspace X");
+        if (st >= 1 && big_alloc(&g->S, bytes, g->stream) != cudaSuccess)
+            return fail_cuda(cudaErrorMemoryAllocation, "workspace S");
+        if (st >= 2 && big_alloc(&g->T, bytes, g->stream) != cudaSuccess)
+            return fail_cuda(cudaErrorMemoryAllocation, "workspace T");
         g->ws_prec = prec;
         g->ws_st = st;
     }
@@ -745,7 +800,7 @@ int start_solve(lsfft_grid* g, int st) {
 void abandon_solve(lsfft_grid* g) {
     cudaStreamSynchronize(g->stream);
     cudaGetLastError();
-    if (g->cur_E) cudaFree(g->cur_E);
+    big_free(g->cur_E);
     g->cur_E = nullptr;
     g->phase = 0;
     g->phase_finish = false;
@@ -847,7 +902,7 @@ int poll_solve(lsfft_grid* g) {
         // output pass: E of the last iterate, its sigma_* and averages, history
         g->cur_kernels += 4;   // output row pass, finalize, two readbacks
         const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
-        CK(cudaMallocAsync(&g->cur_E, ebytes, g->stream));
+        CK(big_alloc(&g->cur_E, ebytes, g->stream));
         CK(launch_row<T>(g, g->cur_st, MODE_ROW_OUTPUT, (cx<T>*)g->cur_E));
         CK(launch_finalize(g->partials, g->cur_nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1,
                            g->stream));
@@ -921,9 +976,9 @@ void lsfft_destroy_grid(lsfft_grid* g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     clear_graphs(g);
     cudaFree(g->mask);
-    cudaFree(g->X);
-    cudaFree(g->S);
-    cudaFree(g->T);
+    big_free(g->X);
+    big_free(g->S);
+    big_free(g->T);
     cudaFree(g->partials);
     cudaFree(g->hist);
     cudaFree(g->ctrl_dev);
@@ -938,7 +993,7 @@ void lsfft_destroy_grid(lsfft_grid* g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     if (g->ev_check) cudaEventDestroy(g->ev_check);
     if (g->hist_host) cudaFreeHost(g->hist_host);
-    if (g->cur_E) cudaFree(g->cur_E);
+    big_free(g->cur_E);
     cudaFree(g->sigma64);
     cudaFree(g->sigma_t);
     if (g->own_stream) cudaStreamDestroy(g->stream);
@@ -1093,7 +1148,7 @@ int lsfft_launch_passes(lsfft_grid* g, int kind, int count) {
 
 void lsfft_free_result(lsfft_result* res) {
     if (!res) return;
-    if (res->E_device) cudaFree(res->E_device);
+    big_free(res->E_device);
     free(res->hist_sigma_re);
     free(res->hist_sigma_im);
     free(res->hist_rel_change);
