@@ -111,7 +111,13 @@ struct ColCfg {
     static constexpr int EPC = CS / 8;                            // 8-byte tensor elements per value
     static constexpr int item_bytes(int cols) { return D * N * cols * CS; }
     static constexpr int xp() { return roundup16(N + N / 16) + 8; }
-    static constexpr int bytes(int cols) { return 2 * item_bytes(cols) + D * cols * xp() * CS + 64; }
+    // a slot holds the item as the TMA box delivers it (dense), and once the
+    // threads have read it into registers, the padded exchange lines of its
+    // D * cols transforms: no separate exchange buffer
+    static constexpr int slot_bytes(int cols) {
+        return (cmax(item_bytes(cols), D * cols * xp() * CS) + 1023) / 1024 * 1024;
+    }
+    static constexpr int bytes(int cols) { return 2 * slot_bytes(cols) + 64; }
     // adjacent line starts per item: a 32-byte row segment, or 16 bytes when
     // two item buffers of 32-byte segments do not fit.  FP64 2-D columns take
     // one line start per item (16 bytes): the FP64 pipe, not DRAM, bounds them,
@@ -120,6 +126,7 @@ struct ColCfg {
                                 : bytes(32 / CS) <= 220 * 1024 ? 32 / CS : 16 / CS;
     static constexpr int THREADS = D * COLS * TL;                 // every line of an item at once
     static constexpr int ITEM_BYTES = item_bytes(COLS);
+    static constexpr int SLOT_BYTES = slot_bytes(COLS);
     static constexpr int XP = xp();
     static constexpr int BJ0 = N < 256 ? N : 256;                 // TMA box rows: inner and outer dimension
     static constexpr int BJ1 = N / BJ0;
@@ -851,12 +858,11 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
     if (A.ctrl->skipB) return;
     const int mode = A.mode;
 
-    C* Bf = reinterpret_cast<C*>(smem_raw);                                    // [2][D][N][COLS]
+    // two slots, each [D][N][COLS] as loaded, then the exchange lines [D * COLS][XP]
     const int w = threadIdx.x % COLS;
     const int t = (threadIdx.x / COLS) % TL;
     const int c = threadIdx.x / (COLS * TL);                                   // component plane
-    C* Xb = reinterpret_cast<C*>(smem_raw + 2 * Cfg::ITEM_BYTES) + (c * COLS + w) * XP;
-    const uint32_t bar0 = smem_u32(smem_raw + 2 * Cfg::ITEM_BYTES + D * COLS * XP * Cfg::CS);
+    const uint32_t bar0 = smem_u32(smem_raw + 2 * Cfg::SLOT_BYTES);
     const int nx = A.n[0];
     // n_inner need not be a multiple of COLS (the half-spectrum planes hold
     // n_x/2 + 1 columns within a padded pitch): the last group runs into padding
@@ -867,7 +873,7 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
     auto load_item = [&](int64_t item, int b) {   // leader only
         const uint32_t bar = bar0 + 8 * b;
         mbar_expect_tx(bar, Cfg::ITEM_BYTES + A.extra_tx);
-        tma_load_5d(smem_u32(Bf) + b * Cfg::ITEM_BYTES, &A.tmap, (int)((item % cblocks) * COLS * EPC), 0, 0,
+        tma_load_5d(smem_u32(smem_raw) + b * Cfg::SLOT_BYTES, &A.tmap, (int)((item % cblocks) * COLS * EPC), 0, 0,
                     (int)(item / cblocks), 0, bar);
     };
 
@@ -887,14 +893,16 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
         const int b = it & 1;
         const int64_t after = item + 2 * (int64_t)A.grid_blocks;   // the next item for this buffer
         if (!mbar_wait(bar0 + 8 * b, (it >> 1) & 1u, A.wait_limit)) fault = true;
-        C* Bi = Bf + (size_t)b * D * N * COLS;
+        C* Bi = reinterpret_cast<C*>(smem_raw + b * Cfg::SLOT_BYTES);
         C* Yc = Bi + c * N * COLS;                                             // this thread's plane
+        C* Xb = Bi + (c * COLS + w) * XP;                                      // its exchange line
         C v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = Yc[(t + TL * m) * COLS + w];
         if (mode == MODE_COL_GAMMA) {
             // forward transforms, Gamma on every position of the item, inverse transforms
             LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+            __syncthreads();   // the exchange lines share the slot: all reads done
 #pragma unroll
             for (int m = 0; m < E; ++m) Yc[(t + TL * m) * COLS + w] = v[m];
             __syncthreads();
