@@ -158,7 +158,11 @@ int lsfft_copy_field(const lsfft_result *res, void *dst, int dst_on_device);
  * null result, destination or field; ECUDA if the copy cannot be enqueued. */
 int lsfft_copy_field_async(const lsfft_result *res, void *dst, int dst_on_device, void *cuda_stream);
 
-/* Free the result's host history and device field. */
+/* Free the result's host history and device field.  Grid workspaces and result
+ * fields come from a per-device stream-ordered memory pool that keeps freed
+ * blocks for the next grid or solve (no unmap and remap of gigabyte buffers);
+ * the pool returns its memory to the driver once no grid and no result is
+ * alive. */
 void lsfft_free_result(lsfft_result *res);
 
 /* Convergence and stability of EM in H'' (Eq. J4, J43, J46) for sigma_1 and
