@@ -269,3 +269,35 @@ def test_async_field_copy_matches_the_synchronous_copy(L):
         r2.free()
         with pytest.raises(ValueError):
             r1.field_into_async(host.data_ptr(), False, cs.cuda_stream)
+
+
+def test_field_pool_reuses_and_returns_memory(L):
+    """Workspaces and result fields come from a caching pool: repeated solves do
+    not grow the device footprint, and once no grid or result is alive the
+    pool hands its memory back to the driver."""
+    import torch
+
+    n = 4096
+    field = 2 * n * n * 8                       # one complex FP32 [2][N] result field
+    mask = square_array_mask(n)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    g = L.Grid(mask)
+    try:
+        for _ in range(2):
+            g.solve(10.0, [1.0, 0.0], scheme="ms", precision="fp32", tol=0.0, max_iter=2).free()
+        free1 = torch.cuda.mem_get_info()[0]
+        for _ in range(6):
+            g.solve(10.0, [1.0, 0.0], scheme="ms", precision="fp32", tol=0.0, max_iter=2).free()
+        free2 = torch.cuda.mem_get_info()[0]
+        assert abs(free2 - free1) < field // 4, (free1, free2)
+        keep = [g.solve(10.0, [1.0, 0.0], scheme="ms", precision="fp32", tol=0.0, max_iter=2) for _ in range(3)]
+        free3 = torch.cuda.mem_get_info()[0]
+        assert free3 <= free2 - field, (free2, free3)   # two more live fields than before
+        for r in keep:
+            r.free()
+    finally:
+        g.close()
+    torch.cuda.synchronize()
+    free4 = torch.cuda.mem_get_info()[0]
+    assert free4 >= free0 - 64 * 2**20, (free0, free4)
