@@ -77,7 +77,8 @@ def workload_config(args, sigmas):
                     f"MS vs EM-in-H'' (alpha,beta)=(1/4,4), rel. sigma* change {TOL:g} x3, {args.green} Green symbol",
         "n": args.n, "d": 2, "sigma1": list(sigmas), "schemes": list(SCHEMES), "alpha_beta": list(ALPHA_BETA),
         "tol": TOL, "green": args.green, "fields": "FP32 (packed real layout: two half-spectrum planes), FP64 reductions",
-        "l2": "inputs larger than L2 (state 1 GiB per field at 8192^2)",
+        "l2": f"inputs larger than L2: every pass streams the state "
+              f"({2 * (args.n // 2 + 4) * args.n * 8 / 1e9:.2f} GB of half-spectrum planes) against a 129 MB L2",
     }
 
 
