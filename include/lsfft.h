@@ -177,6 +177,23 @@ void lsfft_free_result(lsfft_result *res);
  * 0 < alpha < beta < inf. */
 int lsfft_substitution_rates(lsfft_c128 sigma1, double alpha, double beta, double *rate, double *limit);
 
+/* The full d x d effective conductivity tensor (Eq. J13 read as a tensor
+ * relation <J> = sigma_* <E>, with the paper's remark that the anisotropic case
+ * follows the same way): d solves with the applied fields e_a = unit vectors,
+ * then sigma_* = [<J>_1 ... <J>_d] [<E>_1 ... <E>_d]^-1, formed on the host in
+ * FP64 by Gaussian elimination with partial pivoting.  At the fixed point
+ * <E>_a = e_a and the product is [<J>]; for the Eyre-Milton type schemes,
+ * whose iterates reach <E> = e only in the limit, it is the matrix analogue of
+ * the scalar estimate <J>.e / <E>.e.
+ * out: d*d lsfft_c128, row-major (out[i*d + j] = sigma_ij), host memory.
+ * results: NULL, or d slots that receive the d solves' results (caller frees
+ * each with lsfft_free_result); with NULL the results are freed here.
+ * Returns what the worst solve returned: OK, ENOTCONV or EDIVERGED (out is
+ * still written from the last iterates), or an error (EINVAL, ENOMEM, ECUDA:
+ * out untouched, no result kept).  EINVAL also when [<E>] is singular. */
+int lsfft_effective_tensor(lsfft_grid *grid, lsfft_c128 sigma1, const lsfft_opts *opts, lsfft_c128 *out,
+                           lsfft_result **results);
+
 /* One solve of a batch: grid, sigma_1, applied field (d entries used), options. */
 typedef struct {
     lsfft_grid *grid;
@@ -284,12 +301,16 @@ int lsfft_tridiag_gauss(int m, const double *a, const double *b, double *nodes, 
  * loads the library until the process exits), so N must not exceed
  * 4096 * 65536 = 268,435,456 voxels (EINVAL otherwise).  Every call on a device
  * shares that array and leaves its partial sums in it; calls whose kernels
- * overlap on the GPU race, so serialise them (one stream, or events).  The
- * first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (the only set-up; it allocates nothing): make that
- * first call before any stream capture.  Errors: EINVAL (null pointer, d not
- * in {2, 3}, unknown precision, n[a] < 1, N over the limit), ECUDA (lookup or
- * launch failure); lsfft_noalloc_last_error() gives the message. */
+ * overlap on the GPU race, so serialise them (one stream, or events).  Every
+ * call looks up the array's device address on the current device with
+ * cudaGetSymbolAddress (it allocates nothing; looking it up each time keeps the
+ * address valid across a device reset); the first call on a device, which may
+ * also load the module there, should come before any stream capture.
+ * sigma_* (out[4d+1], out[4d+2]) is NaN when <E>.e = 0.  Errors: EINVAL (null
+ * pointer, d not in {2, 3}, unknown precision, n[a] < 1, N over the limit,
+ * e zero or not finite), ECUDA (lookup failure, or a CUDA error seen right
+ * after a launch, which may also stem from earlier work on the thread: it is
+ * left pending for the caller); lsfft_noalloc_last_error() gives the message. */
 int lsfft_field_averages_noalloc(int d, const int64_t n[3], const void *E_device, int precision,
                                  const uint8_t *mask_device, lsfft_c128 sigma1, const double *e,
                                  double *out_device, void *cuda_stream);

@@ -29,7 +29,7 @@ __all__ = [
     "lsfft_free_result",
     "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
     "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "lsfft_solve_batch", "solve_batch",
-    "lsfft_substitution_rates", "lsfft_debug_inject",
+    "lsfft_substitution_rates", "lsfft_debug_inject", "lsfft_effective_tensor",
     "make_opts",
     "SCHEMES", "GREENS",
 ]
@@ -124,6 +124,8 @@ def load_library():
     lib.lsfft_solve_batch.argtypes = [C.c_int, C.POINTER(_Job), C.POINTER(C.POINTER(_Result)), C.POINTER(C.c_int)]
     lib.lsfft_substitution_rates.argtypes = [_C128, C.c_double, C.c_double, C.POINTER(C.c_double),
                                              C.POINTER(C.c_double)]
+    lib.lsfft_effective_tensor.argtypes = [C.c_void_p, _C128, C.POINTER(Opts), C.POINTER(_C128),
+                                           C.POINTER(C.POINTER(_Result))]
     lib.lsfft_gradient.argtypes = [C.c_void_p, C.POINTER(_Result), C.POINTER(C.c_double), C.c_void_p,
                                    C.POINTER(_C128), C.POINTER(_C128)]
     _lib = lib
@@ -261,6 +263,19 @@ def lsfft_substitution_rates(sigma1: complex, alpha: float, beta: float):
     _check(load_library().lsfft_substitution_rates(_C128(s1.real, s1.imag), float(alpha), float(beta), C.byref(r),
                                                    C.byref(lim)))
     return r.value, lim.value
+
+
+def lsfft_effective_tensor(grid: int, sigma1: complex, opts: Opts, d: int):
+    """(d x d complex tensor, [Result] * d); raises on errors (status other than
+    OK, ENOTCONV, EDIVERGED)."""
+    lib = load_library()
+    out = (_C128 * (d * d))()
+    res = (C.POINTER(_Result) * d)()
+    s1 = complex(sigma1)
+    st = lib.lsfft_effective_tensor(C.c_void_p(grid), _C128(s1.real, s1.imag), C.byref(opts), out, res)
+    _check(st, allowed=(OK, ENOTCONV, EDIVERGED))
+    S = np.array([complex(v.re, v.im) for v in out]).reshape(d, d)
+    return S, [Result(res[a].contents.status, res[a]) for a in range(d)]
 
 
 def lsfft_solve_batch(jobs):
@@ -456,25 +471,10 @@ class Grid:
             lsfft_set_sigma_field(self.handle, a.ctypes.data, False, sigma0)
 
     def effective_tensor(self, sigma1, **kw):
-        """The full d x d effective tensor from d solves with applied fields e_a.
-
-        The problem is linear in e and <J> = sigma_* <E> holds for any mask (Eq. J13),
-        so with the columns <J>_a and <E>_a of the d solves sigma_* = [<J>] [<E>]^-1.
-        <E>_a = e_a at the fixed point; the Eyre-Milton type schemes reach it only in
-        the limit, and the product form is their matrix analogue of the scalar
-        estimate <J>.e / <E>.e.  A mask without square symmetry gives an
-        anisotropic, possibly non-diagonal tensor.  Returns (tensor, results)."""
-        Jm = np.zeros((self.d, self.d), dtype=np.complex128)
-        Em = np.zeros((self.d, self.d), dtype=np.complex128)
-        results = []
-        for a in range(self.d):
-            e = np.zeros(self.d)
-            e[a] = 1.0
-            r = self.solve(sigma1, e, **kw)
-            Jm[:, a] = r.mean_J
-            Em[:, a] = r.mean_E
-            results.append(r)
-        return Jm @ np.linalg.inv(Em), results
+        """The full d x d effective tensor (lsfft_effective_tensor): d solves with
+        applied fields e_a, sigma_* = [<J>] [<E>]^-1 formed in the library.
+        Returns (tensor, results)."""
+        return lsfft_effective_tensor(self.handle, sigma1, make_opts(**kw), self.d)
 
     def gradient(self, result, e, grad_ptr=None):
         """(d sigma_*/d sigma_1, energy estimate); d sigma_*/d sigma(x) into grad_ptr."""

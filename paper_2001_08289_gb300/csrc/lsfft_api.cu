@@ -1586,6 +1586,89 @@ int lsfft_solve_batch(int njobs, const lsfft_job* jobs, lsfft_result** results, 
     return LSFFT_OK;
 }
 
+int lsfft_effective_tensor(lsfft_grid* g, lsfft_c128 sigma1, const lsfft_opts* o, lsfft_c128* out,
+                           lsfft_result** results) {
+    if (!g || !o || !out) {
+        g_last_error = "lsfft_effective_tensor: null argument";
+        return LSFFT_EINVAL;
+    }
+    const int d = g->d;
+    lsfft_result* res[3] = {nullptr, nullptr, nullptr};
+    auto release = [&]() {
+        for (int a = 0; a < d; ++a) lsfft_free_result(res[a]);
+    };
+    // columns a of [<J>] and [<E>]: the solve with applied field e_a
+    cplx Jm[3][3], Em[3][3];
+    int worst = LSFFT_OK;
+    for (int a = 0; a < d; ++a) {
+        double e[3] = {0.0, 0.0, 0.0};
+        e[a] = 1.0;
+        const int rc = lsfft_solve(g, sigma1, e, o, &res[a]);
+        if (!res[a]) {   // an error: nothing to assemble
+            release();
+            return rc;
+        }
+        if (rc != LSFFT_OK && worst != LSFFT_EDIVERGED) worst = rc;
+        for (int i = 0; i < d; ++i) {
+            Jm[i][a] = cplx(res[a]->mean_J[i].re, res[a]->mean_J[i].im);
+            Em[i][a] = cplx(res[a]->mean_E[i].re, res[a]->mean_E[i].im);
+        }
+    }
+    // S [E] = [J]  <=>  [E]^T S^T = [J]^T: solve for the rows of S by elimination
+    // on [E]^T with partial pivoting, all d right-hand sides at once
+    cplx A[3][3], B[3][3];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            A[i][j] = Em[j][i];
+            B[i][j] = Jm[j][i];
+        }
+    double scale = 0.0;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) scale = std::max(scale, std::abs(A[i][j]));
+    for (int c = 0; c < d; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < d; ++r)
+            if (std::abs(A[r][c]) > std::abs(A[piv][c])) piv = r;
+        if (!(std::abs(A[piv][c]) > 1e-14 * scale)) {
+            g_last_error = "lsfft_effective_tensor: the matrix of mean fields <E> is singular";
+            if (results) {
+                for (int a = 0; a < d; ++a) results[a] = nullptr;
+            }
+            release();
+            return LSFFT_EINVAL;
+        }
+        for (int j = 0; j < d; ++j) {
+            std::swap(A[c][j], A[piv][j]);
+            std::swap(B[c][j], B[piv][j]);
+        }
+        for (int r = c + 1; r < d; ++r) {
+            const cplx f = A[r][c] / A[c][c];
+            for (int j = 0; j < d; ++j) {
+                A[r][j] -= f * A[c][j];
+                B[r][j] -= f * B[c][j];
+            }
+        }
+    }
+    cplx X[3][3];   // X = S^T
+    for (int j = 0; j < d; ++j)
+        for (int r = d - 1; r >= 0; --r) {
+            cplx acc = B[r][j];
+            for (int k = r + 1; k < d; ++k) acc -= A[r][k] * X[k][j];
+            X[r][j] = acc / A[r][r];
+        }
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            out[i * d + j].re = X[j][i].real();
+            out[i * d + j].im = X[j][i].imag();
+        }
+    if (results) {
+        for (int a = 0; a < d; ++a) results[a] = res[a];
+    } else {
+        release();
+    }
+    return worst;
+}
+
 int lsfft_substitution_rates(lsfft_c128 sigma1, double alpha, double beta, double* rate, double* limit) {
     if (!(alpha > 0.0 && beta > alpha && std::isfinite(beta)) || !rate || !limit) {
         g_last_error = "lsfft_substitution_rates: need 0 < alpha < beta and output pointers";

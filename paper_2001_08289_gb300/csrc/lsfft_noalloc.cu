@@ -10,7 +10,7 @@
 // __device__ array instead of allocated scratch.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <cmath>
 #include <string>
 
 #include "lsfft.h"
@@ -22,15 +22,11 @@ constexpr int NA_THREADS = 256;
 constexpr int64_t NA_CHUNK = 65536;          // voxels per partial sum
 constexpr int NA_MAX_PARTIALS = 4096;        // so at most 268,435,456 voxels per call
 constexpr int NA_NV = 16;                    // slots per partial (4 d + 1 <= 13 used)
-constexpr int NA_MAX_DEVICES = 64;
 
 // Shared by every call on a device and kept until the process exits (512 KiB).
 // Host code must not use this name as an address: the device address comes
 // from cudaGetSymbolAddress below.
 static __device__ __align__(256) double g_noalloc_scratch[NA_MAX_PARTIALS * NA_NV];
-
-std::mutex g_setup_mutex;
-void* g_scratch_addr[NA_MAX_DEVICES] = {};
 
 thread_local std::string g_noalloc_error;
 
@@ -95,36 +91,35 @@ __global__ void noalloc_finish(const double* __restrict__ scratch, int nparts, i
         je_im += tot[4 * c + 3] * e[c];
     }
     out[4 * d] = tot[12] / (double)N;
+    // sigma_* is undefined when <E>.e vanishes: report NaN rather than divide by zero
     const double den = ee_re * ee_re + ee_im * ee_im;
-    out[4 * d + 1] = (je_re * ee_re + je_im * ee_im) / den;
-    out[4 * d + 2] = (je_im * ee_re - je_re * ee_im) / den;
+    out[4 * d + 1] = den > 0.0 ? (je_re * ee_re + je_im * ee_im) / den : nan("");
+    out[4 * d + 2] = den > 0.0 ? (je_im * ee_re - je_re * ee_im) / den : nan("");
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the lookup is the only set-up; it allocates nothing).
+// Device address of the scratch array on the current device.  It is looked
+// up on every call (the lookup allocates nothing and is cheap), so that an
+// address never outlives a device reset or a rebuilt primary context.
 int scratch_on_current_device(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        g_noalloc_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        g_noalloc_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
         return LSFFT_ECUDA;
     }
-    if (dev < 0 || dev >= NA_MAX_DEVICES) {
-        g_noalloc_error = "device ordinal beyond the supported range";
-        return LSFFT_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            g_noalloc_error = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-            return LSFFT_ECUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = static_cast<double*>(g_scratch_addr[dev]);
+    *out = static_cast<double*>(p);
     return LSFFT_OK;
+}
+
+// Launch check that leaves the thread's error state alone: an error pending from
+// earlier work is reported as such, not as this call's, and the caller's own
+// cudaGetLastError still sees it.
+int check_launch(const char* what) {
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e == cudaSuccess) return LSFFT_OK;
+    g_noalloc_error = std::string("CUDA error after launching ") + what +
+                      " (it may stem from earlier work on this thread): " + cudaGetErrorString(e);
+    return LSFFT_ECUDA;
 }
 
 }  // namespace
@@ -139,6 +134,12 @@ int lsfft_field_averages_noalloc(int d, const int64_t n[3], const void* E_device
     if (!n || !E_device || !mask_device || !e || !out_device || (d != 2 && d != 3) ||
         (precision != LSFFT_FP32 && precision != LSFFT_FP64)) {
         g_noalloc_error = "null pointer, d not in {2, 3} or unknown precision";
+        return LSFFT_EINVAL;
+    }
+    double e2 = 0.0;
+    for (int c = 0; c < d; ++c) e2 += e[c] * e[c];
+    if (!(e2 > 0.0) || !std::isfinite(e2)) {
+        g_noalloc_error = "the applied field e must be finite and non-zero";
         return LSFFT_EINVAL;
     }
     int64_t N = 1;
@@ -164,12 +165,11 @@ int lsfft_field_averages_noalloc(int d, const int64_t n[3], const void* E_device
     else
         noalloc_partials<double><<<nparts, NA_THREADS, 0, s>>>((const double2*)E_device, mask_device, d, N, sigma1.re,
                                                                sigma1.im, scratch);
+    rc = check_launch("the partial-sum kernel");
+    if (rc != LSFFT_OK) return rc;
     noalloc_finish<<<1, 32, 0, s>>>(scratch, nparts, d, N, e[0], e[1], d > 2 ? e[2] : 0.0, out_device);
-    const cudaError_t le = cudaGetLastError();
-    if (le != cudaSuccess) {
-        g_noalloc_error = std::string("launch: ") + cudaGetErrorString(le);
-        return LSFFT_ECUDA;
-    }
+    rc = check_launch("the final-sum kernel");
+    if (rc != LSFFT_OK) return rc;
     return LSFFT_OK;
 }
 

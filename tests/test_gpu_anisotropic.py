@@ -1,5 +1,6 @@
-"""Full effective tensor (d solves, one per applied field e_a) on masks without
-square symmetry, against the FP64 oracle's direct solve and a closed form."""
+"""Full effective tensor (lsfft_effective_tensor: d solves, one per applied field
+e_a, and [<J>][<E>]^-1 in the library) on masks without square symmetry,
+against the FP64 oracle's direct solve and a closed form."""
 import numpy as np
 import pytest
 
@@ -62,3 +63,25 @@ def test_effective_tensor_diagonal_laminate_and_3d(L):
         S3, _ = g.effective_tensor(5.0, scheme="em", precision="fp64", green="fd", tol=1e-14, max_iter=4000)
     assert np.abs(S3 - ref).max() < 1e-10 * np.abs(ref).max()
     assert np.abs(S3 - S3.T).max() < 1e-10  # reciprocity for real sigma_1
+
+
+def test_effective_tensor_without_results_and_with_cap(L):
+    """results = NULL frees the d solves inside the call; a solve that hits max_iter
+    makes the call return ENOTCONV with the tensor of the last iterates."""
+    import ctypes as C
+
+    mask = _rect_mask(32, 32)
+    lib = L.load_library()
+    ref = X.effective_tensor(mask, 4.0, "fd")
+    with L.Grid(mask) as g:
+        out = (L._C128 * 4)()
+        st = lib.lsfft_effective_tensor(C.c_void_p(g.handle), L._C128(4.0, 0.0),
+                                        C.byref(L.make_opts(scheme="ms", precision="fp64", green="fd", tol=1e-14,
+                                                            max_iter=4000)), out, None)
+        assert st == L.OK
+        S = np.array([complex(v.re, v.im) for v in out]).reshape(2, 2)
+        assert np.abs(S - ref).max() < 1e-10 * np.abs(ref).max()
+        st = lib.lsfft_effective_tensor(C.c_void_p(g.handle), L._C128(4.0, 0.0),
+                                        C.byref(L.make_opts(scheme="ms", precision="fp64", green="fd", tol=1e-14,
+                                                            max_iter=3)), out, None)
+        assert st == L.ENOTCONV

@@ -90,3 +90,10 @@ def test_field_copies_reject_null_arguments_without_gpu(lib):
     assert lib.lsfft_copy_field(None, buf, 0) == 1
     assert lib.lsfft_copy_field_async(None, buf, 0, None) == 1
     assert lib.lsfft_copy_field_async(None, None, 1, None) == 1
+
+
+def test_effective_tensor_rejects_null_arguments_without_gpu(lib):
+    lib.lsfft_effective_tensor.argtypes = [ctypes.c_void_p, ctypes.c_double * 2, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]
+    out = ctypes.create_string_buffer(16 * 9)
+    assert lib.lsfft_effective_tensor(None, (ctypes.c_double * 2)(1.0, 0.0), None, out, None) == 1
