@@ -36,7 +36,7 @@ from synth import SIGMA1_SWEEP_2D, square_array_mask  # noqa: E402
 
 METRIC = "voxel-iters/s; time-to-1e-6 σ* accelerated vs basic MS; % HBM roofline"
 UNIT = "voxel-iters/s"
-SCHEMES = ("ms", "em_sub")
+SCHEMES = ("ms", "em", "em_sub")       # basic MS vs Eyre-Milton vs accelerated (EM in H'')
 ALPHA_BETA = (0.25, 4.0)          # the Moulinec-Suquet estimate quoted in the paper
 TOL = 1e-6
 FRACTION = 0.25
@@ -65,16 +65,19 @@ def parse():
                         "64^2 FP64 lattice, the 3-D cubic arrays, the batched complex-sigma_1 sweep and the "
                         "adjoint (gradient) configuration, one JSON line each")
     p.add_argument("--sweep-sigmas", type=int, default=16, help="sweep: sigma_1 values per microstructure per step")
-    p.add_argument("--fd-voxels", type=int, default=16, help="adjoint: voxels checked by central differences")
+    p.add_argument("--fd-voxels", type=int, default=64, help="adjoint: voxels checked by central differences")
     p.add_argument("--fig-iters", type=int, default=600, help="fig5: iteration cap per curve")
     p.add_argument("--dim", type=int, default=2, choices=(2, 3), help="passes: 2-D or 3-D square array")
+    p.add_argument("--plot-dir", default=None,
+                   help="fig5: also write the two convergence plots (SVG) and their data (JSON) here")
     return p.parse_args()
 
 
 def workload_config(args, sigmas):
     return {
         "workload": f"2D square array of squares (f=0.25), {args.n}x{args.n}, sigma1 in {list(sigmas)}, "
-                    f"MS vs EM-in-H'' (alpha,beta)=(1/4,4), rel. sigma* change {TOL:g} x3, {args.green} Green symbol",
+                    f"MS vs EM vs EM-in-H'' (alpha,beta)=(1/4,4), rel. sigma* change {TOL:g} x3, "
+                    f"{args.green} Green symbol",
         "n": args.n, "d": 2, "sigma1": list(sigmas), "schemes": list(SCHEMES), "alpha_beta": list(ALPHA_BETA),
         "tol": TOL, "green": args.green, "fields": "FP32 (packed real layout: two half-spectrum planes), FP64 reductions",
         "l2": f"inputs larger than L2: every pass streams the state "
@@ -183,9 +186,11 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
-# CPU baseline: the FP64 oracle as it stands (single-threaded numpy FFTs)
+# CPU baseline: the FP64 oracle as it stands, its FFTs on every host core
 # ---------------------------------------------------------------------------
-def oracle_sample(n, sigmas, schemes=SCHEMES, updates=1):
+def oracle_sample(n, sigmas, schemes=("ms",), updates=1):
+    """`updates` iterations (sigma_k evaluation + update) of each scheme on the
+    n x n square array; returns (voxel-iterations, seconds)."""
     from oracle import schemes as S
 
     mask = square_array_mask(n)
@@ -203,33 +208,41 @@ def oracle_sample(n, sigmas, schemes=SCHEMES, updates=1):
     return vox, time.perf_counter() - t0
 
 
-def cpu_baseline_block(n=4096):
-    vox, dt = oracle_sample(n, (10.0,))
-    return {"value": vox / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one update (+ sigma_k evaluation) of MS and of EM-in-H'' at sigma1=10 on a {n}x{n} "
-                      f"square array, FP64 numpy (single-threaded FFT), {dt:.1f} s"}
+def oracle_cores():
+    from oracle import fourier
+
+    return int(fourier.WORKERS)
+
+
+def cpu_baseline_block(n=8192, updates=5):
+    vox, dt = oracle_sample(n, (10.0,), updates=updates)
+    return {"value": vox / dt, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+            "sample": f"{updates} MS iterations (sigma_k evaluation + update) at sigma1=10 on the {n}x{n} square "
+                      f"array, FP64 numpy oracle with scipy.fft on {oracle_cores()} threads, {dt:.1f} s"}
 
 
 def run_reference(args, sigmas):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n = 2048
+    n = args.n
+    s1 = sigmas[len(sigmas) // 2]
     for _ in range(args.warmup):
-        oracle_sample(n, (sigmas[len(sigmas) // 2],))
+        oracle_sample(min(n, 2048), (s1,))       # warm-up: imports, FFT plans, page-in
     vox, dt = 0, 0.0
     for _ in range(args.steps):
-        v, t = oracle_sample(n, (sigmas[len(sigmas) // 2],))
+        v, t = oracle_sample(n, (s1,))
         vox += v
         dt += t
     value = vox / dt
-    sample = (f"per step: one update of MS and of EM-in-H'' at sigma1={sigmas[len(sigmas) // 2]} on a {n}x{n} "
-              f"square array (FP64 numpy oracle, single-threaded)")
+    sample = (f"per step: one MS iteration (sigma_k evaluation + update) at sigma1={s1} on the {n}x{n} square "
+              f"array (FP64 numpy oracle, scipy.fft on {oracle_cores()} threads)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex)",
             "data": "synthetic", "config": workload_config(args, sigmas),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -289,10 +302,22 @@ def run_ours(args, sigmas):
             for sch in SCHEMES:
                 r = g.solve(s1, e, scheme=sch, **kw)
                 layout["packed"] = r.packed
-                out.append((s1, sch, r.iterations, r.status, r.sigma_star, r.solve_ms, r.kernel_launches))
+                out.append((s1, sch, r.iterations, r.status, r.sigma_star, r.solve_ms, r.kernel_launches,
+                            r.hist_sigma))
                 r.free()
         return out
 
+    # reference sigma_* per sigma_1 for the true-error counts (untimed): EM in H'' with
+    # FP32 fields run far past the tolerance; FP64 fields are limited to x lines of
+    # 4096 points, so the reference is the median of the last 20 iterates, and their
+    # spread is its own uncertainty
+    refs = {}
+    for s1 in sigmas:
+        r = grid.solve(s1, e, scheme="em_sub", **dict(kw, tol=0.0, max_iter=200))
+        tail = r.hist_sigma[-20:]
+        refs[s1] = (complex(np.median(tail.real), np.median(tail.imag)),
+                    float(np.abs(tail - np.median(tail.real)).max() / abs(np.median(tail.real))))
+        r.free()
     for _ in range(args.warmup):
         step(grid)
     torch.cuda.synchronize()
@@ -313,20 +338,33 @@ def run_ours(args, sigmas):
     torch.cuda.synchronize()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     clk = clocks.stop()
-    vox = sum(it * N for stp in results for (_, _, it, _, _, _, _) in stp)
-    launches = sum(kl for stp in results for (*_, kl) in stp)
+    vox = sum(it * N for stp in results for (_, _, it, *_) in stp)
+    launches = sum(stp_i[6] for stp in results for stp_i in stp)
     if world > 1:
         elapsed, vox = combine_ranks(elapsed, vox, dev)
     value = vox / elapsed
 
-    # per-solve summary of the last timed step: iterations and time to the stop rule
+    # per-solve summary of the last timed step: iterations and time to the stop rule,
+    # and (from the sigma_k history) to a true relative error of 1e-6 against a long
+    # reference run; a solve that hit its iteration cap gives a lower bound only
     last = results[-1]
     per = {}
-    for (s1, sch, it, st, sig, ms, _) in last:
-        per.setdefault(str(s1), {})[sch] = {"iters": it, "status": st, "ms": round(ms, 3),
-                                            "sigma_star": [sig.real, sig.imag]}
-    speed = {k: round(v["ms"]["ms"] / v["em_sub"]["ms"], 3) if "ms" in v and "em_sub" in v else None
-             for k, v in per.items()}
+    for (s1, sch, it, st, sig, ms, _, hist) in last:
+        ref, ref_spread = refs[s1]
+        err = np.abs(hist - ref) / abs(ref)
+        below = np.nonzero(err > TOL)[0]
+        hit = None if (below.size and below[-1] == len(err) - 1) else (int(below[-1]) + 1 if below.size else 0)
+        per.setdefault(str(s1), {})[sch] = {
+            "iters": it, "status": st, "capped": st == 3, "ms": round(ms, 3), "sigma_star": [sig.real, sig.imag],
+            "iters_to_true_1e-6": hit,
+            "ms_to_true_1e-6": None if hit is None else round(ms * (hit + 1) / (it + 1), 3)}
+    speed = {}
+    for k, v in per.items():
+        for other in ("ms", "em"):
+            key = f"{other}_over_em_sub"
+            if other in v and "em_sub" in v:
+                r = round(v[other]["ms"] / v["em_sub"]["ms"], 3)
+                speed.setdefault(key, {})[k] = r if not v[other]["capped"] else f">= {r} ({other} capped at 500)"
     # pass timing with CUDA events on the grid's stream
     passes = {}
     peak, peak_kind = measured_peaks()
@@ -354,6 +392,12 @@ def run_ours(args, sigmas):
             "frac": passes[dom]["frac_of_measured_hbm"], "traffic": ncu_traffic(kname, wl),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
             "per_launch_alg_bytes": passes[dom]["alg_bytes"], "per_launch_ms": passes[dom]["ms"]}
+
+    # comparison only: the same MS update written with torch.fft (cuFFT), per update
+    cufft = cufft_ms_update(n, green=args.green)
+    ours_ms = passes["row_pass|ms"]["ms"] + passes["col_pass|ms"]["ms"]
+    cufft["ours_ms_per_update"] = round(ours_ms, 4)
+    cufft["speedup_ours_vs_cufft"] = round(cufft["ms_per_update"] / ours_ms, 2)
 
     # end to end through the C ABI: pinned host mask in, pinned host fields out.
     # Each solve's field goes to one of two pinned host buffers on a copy stream
@@ -421,10 +465,16 @@ def run_ours(args, sigmas):
             "data": "synthetic", "layout": "packed real (E_x + i E_y in one complex plane)" if layout["packed"]
             else "complex component planes",
             "config": workload_config(args, sigmas), "roofline": roof, "gpu_launches": int(launches),
-            "clocks": clk, "e2e": e2e, "time_to_tol": {"per_sigma1": per, "ms_over_em_sub_time_ratio": speed},
-            "passes": passes}
+            "clocks": clk, "e2e": e2e,
+            "time_to_tol": {"per_sigma1": per, "time_ratio": speed,
+                            "true_error_reference": {str(k): {"sigma_star": [v[0].real, v[0].imag], "spread": v[1]}
+                                                     for k, v in refs.items()},
+                            "note": "iters_to_true_1e-6: first iterate from which |sigma_k - ref|/|ref| stays "
+                                    "<= 1e-6, ref = median of the last 20 of 200 EM-in-H'' iterates (FP32 fields, "
+                                    "FP64 reductions); 'capped' solves stopped at max_iter = 500"},
+            "passes": passes, "cufft_comparison": cufft}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_block()
+        line["cpu_baseline"] = cpu_baseline_block(args.n)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -557,7 +607,9 @@ def run_cube3d(args):
 def run_sweep(args):
     """Batched complex-sigma_1 sweep: 32 RSA-disk microstructures (n in 128..1024, 8
     each), sigma_1 = r e^{i theta}, EM in H'' with per-microstructure Lanczos
-    alpha, beta; all solves of a step go through one lsfft_solve_batch call."""
+    alpha, beta; all solves of a step run in one persistent launch
+    (lsfft_solve_sweep).  The same jobs through the host-scheduled batch
+    (lsfft_solve_batch, one stream per grid) are timed once for comparison."""
     from synth import complex_sigma_ray, rsa_disk_mask
 
     torch, L = _gpu_setup()
@@ -572,6 +624,8 @@ def run_sweep(args):
         vox_n.append(m.size)
     allsig = complex_sigma_ray(count=512, seed=1000)
 
+    host_scheduled = False
+
     def step(k):
         sig = allsig[(k * args.sweep_sigmas) % 512:][:args.sweep_sigmas]
         jobs = []
@@ -581,13 +635,22 @@ def run_sweep(args):
                 rate, limit = L.lsfft_substitution_rates(s1, a, b)
                 sch = "em_sub" if rate < 0.98 * limit else "em"
                 jobs.append((g, s1, [1.0, 0.0], dict(scheme=sch, green="fd", tol=TOL, max_iter=400, alpha=a, beta=b)))
-        out = L.solve_batch(jobs)
+        out = (L.solve_batch if host_scheduled else L.solve_sweep)(jobs)
         vox = sum(r.iterations * jobs[i][0].N for i, r in enumerate(out) if not isinstance(r, Exception))
         st = [(jobs[i][3]["scheme"], getattr(r, "status", -1)) for i, r in enumerate(out)]
         for r in out:
             if not isinstance(r, Exception):
                 r.free()
         return vox, len(jobs), st
+
+    host_scheduled = True   # comparison: one timed step of the host-scheduled batch
+    step(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hv, hn, _ = step(1)
+    torch.cuda.synchronize()
+    host_rate = hv / (time.perf_counter() - t0)
+    host_scheduled = False
 
     for k in range(args.warmup):
         step(k)
@@ -611,8 +674,10 @@ def run_sweep(args):
                        f"(plain EM where EM-in-H'' is not rounding-stable), tol {TOL:g}, FP32, at most 400 "
                        f"iterations",
            "solves_per_step": solves // max(args.steps, 1)},
-          dtype="c64", solves_per_s=solves / dt, ms_per_step=1e3 * dt / args.steps,
-          status_counts={f"{sch}:{st}": statuses.count((sch, st)) for sch, st in sorted(set(statuses))})
+          dtype="c64", solves_per_s=solves / dt, ms_per_step=1e3 * dt / args.steps, gpu_launches_per_step=1,
+          status_counts={f"{sch}:{st}": statuses.count((sch, st)) for sch, st in sorted(set(statuses))},
+          host_scheduled_batch_voxel_iters_per_s=host_rate,
+          executor="one persistent launch per step (lsfft_solve_sweep): device work queue over (solve, pass, item)")
 
 
 def run_adjoint(args):
@@ -668,38 +733,42 @@ def run_adjoint(args):
           fd_median_rel_err=float(np.median(errs)))
 
 
-def run_cufft(args):
-    """Comparison only: the same Moulinec-Suquet update on the same 8192^2 square
-    array written with torch.fft (cuFFT real-to-complex transforms) and torch
-    elementwise kernels, FP32, trig symbol, sigma_1 = 10: tau = (sigma/sigma_0 - 1) E,
-    E^ = -Gamma tau^ (zero mode N e, Nyquist lines zero), E = inverse FFT, and the
-    average <sigma E> per update.  Fixed iteration count, CUDA events."""
-    torch, L = _gpu_setup()
-    n = args.n
-    dev = torch.device("cuda", 0)
+def cufft_ms_update(n, green="trig", iters=30, s1=10.0):
+    """Comparison only: the Moulinec-Suquet update on the n x n square array written
+    with torch.fft (cuFFT real-to-complex transforms) and torch elementwise kernels,
+    FP32, sigma_1 = 10: tau = (sigma/sigma_0 - 1) E, E^ = -Gamma tau^ (zero mode N e,
+    Nyquist lines zero for the trig symbol), E = inverse FFT, and <sigma E> per
+    update.  Fixed iteration count, CUDA events.  Returns a dict."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
     mask = torch.from_numpy(square_array_mask(n)).to(dev)
-    s1, s0 = 10.0, (10.0 + 1.0) / 2
+    s0 = (s1 + 1.0) / 2
     a = torch.where(mask != 0, torch.tensor(s1 / s0 - 1, device=dev), torch.tensor(1 / s0 - 1, device=dev))
     sig = torch.where(mask != 0, torch.tensor(s1, device=dev), torch.tensor(1.0, device=dev))
     ky = torch.fft.fftfreq(n, d=1.0 / n, device=dev).round().view(n, 1)
     kx = torch.arange(n // 2 + 1, device=dev, dtype=torch.float32).view(1, n // 2 + 1)
-    nyq = (ky == -(n // 2)) | (kx == n // 2)
-    k2 = kx * kx + ky * ky
-    inv = torch.where((k2 > 0) & ~nyq, 1.0 / k2.clamp(min=1.0), torch.zeros_like(k2))
+    if green == "trig":
+        ux, uy = kx.to(torch.complex64), ky.to(torch.complex64)
+        nyq = (ky == -(n // 2)) | (kx == n // 2)
+    else:
+        ux = torch.exp(2j * math.pi * kx / n) - 1
+        uy = torch.exp(2j * math.pi * ky / n) - 1
+        nyq = torch.zeros_like(kx * ky, dtype=torch.bool)
+    k2 = (ux.abs() ** 2 + uy.abs() ** 2)
+    inv = torch.where((k2 > 0) & ~nyq, 1.0 / k2.clamp(min=1e-30), torch.zeros_like(k2))
     E = torch.zeros((2, n, n), device=dev, dtype=torch.float32)
     E[0] = 1.0
 
     def update(E):
         T = torch.fft.rfft2(a * E)
-        proj = (kx * T[0] + ky * T[1]) * inv
-        Eh = torch.stack((-kx * proj, -ky * proj))
+        proj = (ux.conj() * T[0] + uy.conj() * T[1]) * inv
+        Eh = torch.stack((-ux * proj, -uy * proj))
         Eh[0, 0, 0] = n * n * 1.0
         Eh[1, 0, 0] = 0.0
         E = torch.fft.irfft2(Eh, s=(n, n))
-        sigma_k = (sig * E[0]).mean()
-        return E, sigma_k
+        return E, (sig * E[0]).mean()
 
-    iters = 30
     for _ in range(3):
         E, sk = update(E)
     torch.cuda.synchronize()
@@ -710,10 +779,17 @@ def run_cufft(args):
     t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / iters
-    _line("voxel-iters/s (torch.fft / cuFFT comparison, MS update)", n * n / (ms / 1e3), UNIT, args,
-          {"workload": f"{n}x{n} square array, sigma1 = 10, MS update with torch.fft.rfft2/irfft2 (cuFFT) and torch "
-                       "elementwise kernels, FP32, trig symbol; comparison only, not the library's path", "n": n},
-          dtype="f32", ms_per_update=round(ms, 4), sigma_k=float(sk))
+    return {"ms_per_update": round(ms, 4), "voxel_iters_per_s": n * n / (ms / 1e3), "sigma_k": float(sk),
+            "what": f"MS update, sigma1={s1}, {n}x{n}, torch.fft.rfft2/irfft2 (cuFFT) + torch elementwise kernels, "
+                    f"FP32, {green} symbol; comparison only, not the library's path"}
+
+
+def run_cufft(args):
+    """Comparison only: the same Moulinec-Suquet update with torch.fft (cuFFT)."""
+    torch, L = _gpu_setup()
+    c = cufft_ms_update(args.n, green=args.green)
+    _line("voxel-iters/s (torch.fft / cuFFT comparison, MS update)", c["voxel_iters_per_s"], UNIT, args,
+          {"workload": c["what"], "n": args.n}, dtype="f32", ms_per_update=c["ms_per_update"], sigma_k=c["sigma_k"])
 
 
 def run_precision(args):
@@ -791,6 +867,43 @@ def run_passes(args):
           dtype="f32" if d == 2 else "c64", higher_is_better=False, passes=out)
 
 
+def write_convergence_svg(path, title, curves, floor=1e-12, width=640, height=420):
+    """A log-scale line plot of error against iteration, as plain SVG text.
+    curves: {label: (list of errors, colour, dash)}."""
+    ml, mr, mt, mb = 70, 170, 40, 50
+    pw, ph = width - ml - mr, height - mt - mb
+    kmax = max(len(c[0]) for c in curves.values()) - 1
+    lo, hi = math.floor(math.log10(floor)), 0
+    X = lambda k: ml + pw * k / max(kmax, 1)
+    Y = lambda v: mt + ph * (hi - math.log10(max(v, floor))) / (hi - lo)
+    out = [f'<svg xmlns="http://www.w3.org/2000/svg" width="{width}" height="{height}" '
+           f'font-family="sans-serif" font-size="12">',
+           f'<rect width="{width}" height="{height}" fill="white"/>',
+           f'<text x="{ml}" y="22" font-size="14">{title}</text>',
+           f'<rect x="{ml}" y="{mt}" width="{pw}" height="{ph}" fill="none" stroke="black"/>']
+    for dec in range(lo, hi + 1, 2):
+        y = Y(10.0 ** dec)
+        out.append(f'<line x1="{ml}" y1="{y:.1f}" x2="{ml + pw}" y2="{y:.1f}" stroke="#ddd"/>')
+        out.append(f'<text x="{ml - 8}" y="{y + 4:.1f}" text-anchor="end">1e{dec}</text>')
+    step = max(1, int(round(kmax / 8 / 5.0)) * 5)
+    for k in range(0, kmax + 1, step):
+        out.append(f'<text x="{X(k):.1f}" y="{mt + ph + 18}" text-anchor="middle">{k}</text>')
+    out.append(f'<text x="{ml + pw / 2}" y="{height - 10}" text-anchor="middle">iteration k</text>')
+    out.append(f'<text x="16" y="{mt + ph / 2}" transform="rotate(-90 16 {mt + ph / 2})" text-anchor="middle">'
+               f'|sigma_k - sigma_*| / sigma_*</text>')
+    for i, (label, (ys, colour, dash)) in enumerate(curves.items()):
+        pts = " ".join(f"{X(k):.1f},{Y(v):.1f}" for k, v in enumerate(ys))
+        da = f' stroke-dasharray="{dash}"' if dash else ""
+        out.append(f'<polyline points="{pts}" fill="none" stroke="{colour}" stroke-width="1.6"{da}/>')
+        ly = mt + 16 + 18 * i
+        out.append(f'<line x1="{ml + pw + 12}" y1="{ly}" x2="{ml + pw + 36}" y2="{ly}" stroke="{colour}" '
+                   f'stroke-width="1.6"{da}/>')
+        out.append(f'<text x="{ml + pw + 42}" y="{ly + 4}">{label}</text>')
+    out.append("</svg>")
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+
+
 def run_fig5(args):
     """The Moulinec-Suquet experiment of the section on their numerical example:
     square array of squares at 25 %, sigma_1 = 0 (insulating squares), sigma_2 = 1,
@@ -836,6 +949,20 @@ def run_fig5(args):
                     "curve_rel_err_vs_limit": [float(f"{x:.3g}") for x in err[:200]]}
                 r.free()
     dt = time.perf_counter() - t0
+    if args.plot_dir:
+        os.makedirs(args.plot_dir, exist_ok=True)
+        style = {"fd": ("", ""), "trig": ("4,3", " (trig)")}
+        for fig, pair in (("fig5b_ms_vs_ms_sub", ("ms", "ms_sub")), ("fig5c_em_vs_em_sub", ("em", "em_sub"))):
+            curves = {}
+            for green in ("fd", "trig"):
+                dash, suffix = style[green]
+                for sch, colour in zip(pair, ("#1f4e9c", "#c0392b")):
+                    name = {"ms": "MS", "ms_sub": "MS in H''", "em": "EM (ref. 1/2)", "em_sub": "EM in H''"}[sch]
+                    curves[name + suffix] = (out[f"{green}|{sch}"]["curve_rel_err_vs_limit"][:80], colour, dash)
+            write_convergence_svg(os.path.join(args.plot_dir, f"{fig}_square{n}_sigma1_0.svg"),
+                                  f"sigma_1 = 0, [alpha, beta] = [1/4, 4], {n}x{n} square array, FP64", curves)
+        with open(os.path.join(args.plot_dir, f"fig5_square{n}_sigma1_0_curves.json"), "w") as f:
+            json.dump({k: {kk: vv for kk, vv in v.items()} for k, v in out.items()}, f, indent=0)
     _line("iterations to a relative sigma_* error (sigma_1 = 0 experiment)", vox / dt, UNIT, args,
           {"workload": f"{n}x{n} square array of squares (f = 1/4), sigma_1 = 0, sigma_2 = 1, e = (1, 0), "
                        "[alpha, beta] = [1/4, 4], FP64, fd and trig Green symbols; EM with reference 1/2 "

@@ -99,7 +99,9 @@ typedef struct {
     int packed;                /* 1 if the packed real layout was used: 2-D with every scheme
                                   coefficient real (real sigma_1, real reference medium); the
                                   state then holds the x-spectra of the two real components
-                                  as two half-spectrum planes (E_device is complex as always) */
+                                  as two half-spectrum planes (E_device is complex as always);
+                                  2 if, in addition, the split layout of long columns ran
+                                  (lsfft_set_column_split)                                    */
     int precision;             /* precision of E_device                                     */
     int d;
     int64_t n[3];
@@ -194,6 +196,35 @@ int lsfft_substitution_rates(lsfft_c128 sigma1, double alpha, double beta, doubl
 int lsfft_effective_tensor(lsfft_grid *grid, lsfft_c128 sigma1, const lsfft_opts *opts, lsfft_c128 *out,
                            lsfft_result **results);
 
+/* Strided-pass layout of long 2-D columns (the paper has no counterpart; a
+ * tuning control).  It applies to 2-D grids with n_x, n_y in {4096, 8192} whose
+ * solves run FP32 fields with real coefficients (the packed real layout).
+ * split = 1 (default): the row pass works on row pairs (j, j + n_y/2) and applies
+ * the first radix-2 step of every y-DFT (decimation in frequency), so the
+ * strided pass transforms independent columns of n_y/2 points on one SM each.
+ * split = 0: the strided pass transforms whole columns on two-block clusters
+ * that exchange half-transforms through distributed shared memory.  Both give
+ * the same iterates up to rounding.  Takes effect from the next solve or
+ * lsfft_prepare; waits for the grid's pending work.  EINVAL for a null grid. */
+int lsfft_set_column_split(lsfft_grid *grid, int split);
+
+/* Tuning of a grid's solve (the paper has no counterpart).  Candidates: the
+ * number of updates per CUDA-graph launch between host checks (check_every in
+ * {4, 8, 16, 32, 64}) and, where both exist (lsfft_set_column_split), the split
+ * or cluster strided pass.  Each candidate runs `iters` updates of the given
+ * problem (tol 0, after one untimed run that captures its graph) and is timed
+ * with CUDA events on the grid's stream; the fastest is applied to the grid
+ * (column split) and returned.  opts: the solve's options (scheme, precision,
+ * Green symbol, alpha, beta; its check_every, tol and max_iter are ignored). */
+typedef struct {
+    int check_every;       /* updates per graph launch of the fastest candidate        */
+    int column_split;      /* 1 split layout, 0 cluster pass (or the only layout)      */
+    double ms_per_iter;    /* its device time per update, ms                           */
+    int candidates;        /* configurations timed                                     */
+} lsfft_tuning;
+int lsfft_autotune(lsfft_grid *grid, lsfft_c128 sigma1, const double *e, const lsfft_opts *opts, int iters,
+                   lsfft_tuning *out);
+
 /* One solve of a batch: grid, sigma_1, applied field (d entries used), options. */
 typedef struct {
     lsfft_grid *grid;
@@ -211,6 +242,25 @@ typedef struct {
  * LSFFT_OK once every job has finished, or EINVAL (with nothing run) for null
  * arrays or a job without grid.  Grids must not be used elsewhere meanwhile. */
 int lsfft_solve_batch(int njobs, const lsfft_job *jobs, lsfft_result **results, int *statuses);
+
+/* Run a batch of solves in one persistent kernel launch (the batched sweep over
+ * sigma_1 and microstructures of uneven sizes; section "Estimating the
+ * parameters alpha and beta" for the alpha, beta per microstructure, Eq. J3
+ * for complex sigma_1).  Every job: a 2-D grid with n_x, n_y powers of two in
+ * [128, 1024], a two-phase medium (no lsfft_set_sigma_field), FP32 fields, any
+ * scheme and Green symbol.  A device work queue hands out items (a few rows of
+ * a row pass, a few columns of a strided pass) of every solve to the resident
+ * blocks; the block that completes a solve's pass takes the solve to its next
+ * pass (row pass -> FP64 finalize and stop rule -> strided pass -> row pass,
+ * and the output pass once the stop rule fired), so solves of all sizes and
+ * iteration counts progress side by side with no host involvement.  The
+ * batch (descriptors in, the launch, results out) is one captured CUDA graph.
+ * results[j] / statuses[j] as for lsfft_solve (complex layout fields, FP32);
+ * each result's solve_ms is the device time of the whole batch and its
+ * kernel_launches is 1.  Returns EINVAL (nothing run) if a job does not
+ * qualify, ECUDA if a block of the launch found no work for two seconds while
+ * solves remained (no result is kept), else OK. */
+int lsfft_solve_sweep(int njobs, const lsfft_job *jobs, lsfft_result **results, int *statuses);
 
 /* Per-voxel conductivity sigma(x) (complex, N entries, host or device
  * pointer; copied).  Subsequent solves on the grid use sigma(x) instead of the

@@ -8,9 +8,10 @@ and the CPU-baseline leg of ``bench.py`` use it.  It shares no code with the
 CUDA path; both sides draw their inputs from the seeded generators in
 ``synth``.
 
-The oracle is plain and slow on purpose: numpy FFTs (pinned against a brute
-force DFT), the Green operator written out per frequency from Eq. J11, the four
-schemes written step by step in the paper's notation, and an exact discrete
+The oracle is plain and slow on purpose: library FFTs (scipy.fft on every
+host core, pinned against a brute-force DFT), the Green operator written out
+per frequency from Eq. J11, the four schemes written step by step in the
+paper's notation, and an exact discrete
 solution by a dense direct solve whose eigen-decomposition gives the poles of
 sigma_*(sigma_1).
 

@@ -26,9 +26,16 @@ Green symbols
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
+import scipy.fft as _sfft
 
 GREENS = ("trig", "fd")
+
+# Threads of the FFT library: every host core (the transforms are the plain
+# library routine; only their threading changes, not the arithmetic).
+WORKERS = os.cpu_count() or 1
 
 
 def integer_freqs(n: int) -> np.ndarray:
@@ -55,13 +62,13 @@ def spatial_axes(d: int):
 def fft(field: np.ndarray) -> np.ndarray:
     """Unnormalised forward DFT of every component over the spatial axes."""
     d = field.ndim - 1
-    return np.fft.fftn(field, axes=spatial_axes(d))
+    return _sfft.fftn(field, axes=spatial_axes(d), workers=WORKERS)
 
 
 def ifft(field_hat: np.ndarray) -> np.ndarray:
     """Inverse DFT (with the 1/N factor) of every component."""
     d = field_hat.ndim - 1
-    return np.fft.ifftn(field_hat, axes=spatial_axes(d))
+    return _sfft.ifftn(field_hat, axes=spatial_axes(d), workers=WORKERS)
 
 
 def brute_force_dft(f: np.ndarray, inverse: bool = False) -> np.ndarray:

@@ -29,7 +29,9 @@ __all__ = [
     "lsfft_free_result",
     "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
     "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "lsfft_solve_batch", "solve_batch",
-    "lsfft_substitution_rates", "lsfft_debug_inject", "lsfft_effective_tensor",
+    "lsfft_solve_sweep", "solve_sweep",
+    "lsfft_substitution_rates", "lsfft_debug_inject", "lsfft_effective_tensor", "lsfft_set_column_split",
+    "lsfft_autotune",
     "make_opts",
     "SCHEMES", "GREENS",
 ]
@@ -63,6 +65,12 @@ class Opts(C.Structure):
     _fields_ = [("scheme", C.c_int), ("precision", C.c_int), ("green", C.c_int), ("max_iter", C.c_int),
                 ("stop_consecutive", C.c_int), ("check_every", C.c_int), ("tol", C.c_double),
                 ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class _Tuning(C.Structure):
+    """Mirror of lsfft_tuning."""
+    _fields_ = [("check_every", C.c_int), ("column_split", C.c_int), ("ms_per_iter", C.c_double),
+                ("candidates", C.c_int)]
 
 
 class _Job(C.Structure):
@@ -121,7 +129,11 @@ def load_library():
                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.lsfft_set_sigma_field.argtypes = [C.c_void_p, C.c_void_p, C.c_int, _C128]
     lib.lsfft_debug_inject.argtypes = [C.c_void_p, C.c_int]
+    lib.lsfft_set_column_split.argtypes = [C.c_void_p, C.c_int]
+    lib.lsfft_autotune.argtypes = [C.c_void_p, _C128, C.POINTER(C.c_double), C.POINTER(Opts), C.c_int,
+                                   C.POINTER(_Tuning)]
     lib.lsfft_solve_batch.argtypes = [C.c_int, C.POINTER(_Job), C.POINTER(C.POINTER(_Result)), C.POINTER(C.c_int)]
+    lib.lsfft_solve_sweep.argtypes = lib.lsfft_solve_batch.argtypes
     lib.lsfft_substitution_rates.argtypes = [_C128, C.c_double, C.c_double, C.POINTER(C.c_double),
                                              C.POINTER(C.c_double)]
     lib.lsfft_effective_tensor.argtypes = [C.c_void_p, _C128, C.POINTER(Opts), C.POINTER(_C128),
@@ -278,6 +290,39 @@ def lsfft_effective_tensor(grid: int, sigma1: complex, opts: Opts, d: int):
     return S, [Result(res[a].contents.status, res[a]) for a in range(d)]
 
 
+def _job_array(jobs):
+    n = len(jobs)
+    arr = (_Job * max(n, 1))()
+    for i, (h, s1, e, o) in enumerate(jobs):
+        s1 = complex(s1)
+        arr[i].grid = h
+        arr[i].sigma1 = _C128(s1.real, s1.imag)
+        ev = list(e) + [0.0] * (3 - len(e))
+        for c in range(3):
+            arr[i].e[c] = float(ev[c])
+        arr[i].opts = o
+    return arr
+
+
+def lsfft_solve_sweep(jobs):
+    """The batch in one persistent launch (lsfft_solve_sweep).  jobs: list of (grid
+    handle, sigma1, e, Opts).  Returns [(status, result pointer or None)]."""
+    n = len(jobs)
+    arr = _job_array(jobs)
+    res = (C.POINTER(_Result) * max(n, 1))()
+    st = (C.c_int * max(n, 1))()
+    _check(load_library().lsfft_solve_sweep(n, arr, res, st))
+    return [(st[i], res[i] if res[i] else None) for i in range(n)]
+
+
+def solve_sweep(jobs):
+    """jobs: list of (Grid, sigma1, e, kwargs for make_opts).  Returns [Result or LsfftError]."""
+    out = []
+    for st, ptr in lsfft_solve_sweep([(g.handle, s1, e, make_opts(**kw)) for g, s1, e, kw in jobs]):
+        out.append(Result(st, ptr) if ptr else LsfftError(st, lsfft_strerror(st)))
+    return out
+
+
 def lsfft_solve_batch(jobs):
     """jobs: list of (grid handle, sigma1, e, Opts).  Returns [(status, result pointer or None)]."""
     n = len(jobs)
@@ -310,6 +355,20 @@ def lsfft_set_sigma_field(grid: int, sigma_ptr, on_device: bool, sigma0: complex
     s0 = complex(sigma0)
     _check(load_library().lsfft_set_sigma_field(C.c_void_p(grid), C.c_void_p(sigma_ptr) if sigma_ptr else None,
                                                 int(bool(on_device)), _C128(s0.real, s0.imag)))
+
+
+def lsfft_set_column_split(grid: int, split: bool) -> None:
+    _check(load_library().lsfft_set_column_split(C.c_void_p(grid), int(bool(split))))
+
+
+def lsfft_autotune(grid: int, sigma1: complex, e, opts: Opts, iters: int = 32) -> dict:
+    ev = (C.c_double * 3)(*[float(x) for x in list(e) + [0.0] * (3 - len(e))])
+    s1 = complex(sigma1)
+    out = _Tuning()
+    _check(load_library().lsfft_autotune(C.c_void_p(grid), _C128(s1.real, s1.imag), ev, C.byref(opts), int(iters),
+                                         C.byref(out)))
+    return {"check_every": out.check_every, "column_split": out.column_split, "ms_per_iter": out.ms_per_iter,
+            "candidates": out.candidates}
 
 
 def lsfft_debug_inject(grid: int, kind: int) -> None:
@@ -349,7 +408,7 @@ class Result:
         self.hist_field_norm = np.array([r.hist_field_norm[k] for k in range(L)])
         self.solve_ms = float(r.solve_ms)
         self.kernel_launches = int(r.kernel_launches)
-        self.packed = bool(r.packed)
+        self.packed = int(r.packed)    # 0 complex, 1 packed real, 2 packed real with the split layout
         self.precision = int(r.precision)
         self._ptr = ptr
 
@@ -483,6 +542,10 @@ class Grid:
     def lanczos_hull(self, e, **kw):
         """(alpha, beta, nodes, weights) of the pole measure seen from chi e."""
         return lsfft_lanczos_hull(self.handle, e, **kw)
+
+    def set_column_split(self, split: bool) -> None:
+        """Strided-pass layout of 4096/8192-point 2-D columns (lsfft_set_column_split)."""
+        lsfft_set_column_split(self.handle, split)
 
     def launch_passes(self, kind: int, count: int) -> None:
         lsfft_launch_passes(self.handle, kind, count)

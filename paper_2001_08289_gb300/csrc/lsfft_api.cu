@@ -19,6 +19,7 @@
 #include "lsfft.h"
 #include "lsfft_kernels.cuh"
 #include "lsfft_misc.h"
+#include "lsfft_sweep.h"
 
 using namespace lsfft;
 using cplx = std::complex<double>;
@@ -145,6 +146,8 @@ struct lsfft_grid {
     void* fd[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // FD symbol per axis, FP32/FP64
     bool prepared[2] = {false, false};
     int packed = 0;                 // packed real layout for the current solve
+    int split = 0;                  // packed FP32 2-D with n_y >= 4096: split layout (lsfft_split.cuh)
+    bool no_split = false;          // lsfft_set_layout: keep the cluster strided pass instead
     // solve in flight (begin_solve / poll_solve)
     int phase = 0;                  // 0 idle, 1 in flight
     bool phase_finish = false;      // the output pass has been enqueued
@@ -196,8 +199,18 @@ int64_t persistent_blocks(const lsfft_grid* g, int64_t n_items, int blocks_per_s
     return n_items < cap ? n_items : cap;
 }
 
+// The split layout of long 2-D columns: FP32 packed fields, n_x and n_y in {4096, 8192}.
+bool split_shape(const lsfft_grid* g) {
+    return g->d == 2 && (g->n[0] == 4096 || g->n[0] == 8192) && (g->n[1] == 4096 || g->n[1] == 8192);
+}
+
 // Number of row-pass blocks (= partial-sum rows), valid after the kernels were prepared.
 int row_blocks(const lsfft_grid* g, int prec) {
+    if (g->split && prec == LSFFT_FP32) {
+        Geom geo;
+        split_row_dispatch(g->logn[0], OP_QUERY, nullptr, nullptr, &geo);
+        return (int)persistent_blocks(g, g->n[1] / 2, geo.blocks_per_sm);
+    }
     const Geom geo = row_geom(g, prec);
     const int64_t rows = g->N / g->n[0];
     return (int)persistent_blocks(g, (rows + geo.per_block - 1) / geo.per_block, geo.blocks_per_sm);
@@ -221,6 +234,10 @@ int prepare_kernels(lsfft_grid* g) {
     if (g->d == 2) {
         CK(row_dispatch<T, 2>(g->logn[0], OP_PREPARE, nullptr, nullptr, nullptr));
         CK(col_dispatch<T, 2>(g->logn[1], OP_PREPARE, nullptr, nullptr, nullptr));
+        if (sizeof(T) == 4 && split_shape(g)) {
+            CK(split_row_dispatch(g->logn[0], OP_PREPARE, nullptr, nullptr, nullptr));
+            CK(split_col_dispatch(g->logn[1] - 1, OP_PREPARE, nullptr, nullptr, nullptr));
+        }
     } else {
         CK(row_dispatch<T, 3>(g->logn[0], OP_PREPARE, nullptr, nullptr, nullptr));
         CK(col_dispatch<T, 3>(g->logn[1], OP_PREPARE, nullptr, nullptr, nullptr));
@@ -553,6 +570,11 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
     A.k = make_kconst<T>(*g->prm_host);
     A.ctrl = g->ctrl_dev;
     A.partials = g->partials;
+    A.prm = *g->prm_host;
+    A.hist = g->hist;
+    // the row pass runs the finalize step in its last block, except for the
+    // operator of the pole problem (Lanczos), which has no scalar recurrence
+    A.fuse_fin = g->prm_host->scheme != SCHEME_MATVEC ? 1 : 0;
     for (int a = 0; a < 3; ++a) A.fd[a] = a < g->d ? (const cx<T>*)g->fd[a][p] : nullptr;
     A.wait_limit = g->wait_limit;
     A.extra_tx = g->inject_tx;
@@ -564,13 +586,21 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
 }
 
 template <typename T>
-cudaError_t launch_row(lsfft_grid* g, int st, int mode, cx<T>* Eout) {
+cudaError_t launch_row(lsfft_grid* g, int st, int mode, cx<T>* Eout, bool timing_only = false) {
     PassArgs<T> A = base_args<T>(g, st);
+    if (timing_only && A.fuse_fin) A.fuse_fin = 2;   // repeated passes are no iteration: never stop
     A.Eout = Eout;
     A.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[0] : nullptr;
     A.n_lines = g->N / g->n[0];
     A.mode = mode;
     A.grid_blocks = row_blocks(g, sizeof(T) == 4 ? LSFFT_FP32 : LSFFT_FP64);
+    if constexpr (sizeof(T) == 4) {
+        if (g->split) {   // row pairs (j, j + n_y/2); four half-spectrum planes of n_y/2 rows
+            A.n_lines = g->n[1] / 2;
+            A.Nh = A.n_lines * A.hp;
+            return split_row_dispatch(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
+        }
+    }
     if (g->d == 2) return row_dispatch<T, 2>(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
     return row_dispatch<T, 3>(g->logn[0], OP_LAUNCH, &A, g->stream, nullptr);
 }
@@ -640,6 +670,40 @@ cudaError_t encode_col_map(PassArgs<T>* A, int N, int cols, int d) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// TMA view of the four half-spectrum planes of the split layout: 8-byte
+// elements; dimensions (x element within the row pitch, row j0 < 256, row block
+// j1, plane p, half h), so that one box {W columns, 256, M/256, 1, 1} is one
+// plane of W adjacent columns of one half.
+cudaError_t encode_split_map(PassArgs<float>* A, int M, int W) {
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if (M % 256 != 0) return cudaErrorInvalidValue;
+    const cuuint64_t row = (cuuint64_t)A->hp * 8;
+    cuuint64_t dims[5] = {(cuuint64_t)A->hp, 256, (cuuint64_t)(M / 256), 2, 2};
+    cuuint64_t strides[4] = {row, 256 * row, (cuuint64_t)M * row, 2 * (cuuint64_t)M * row};
+    cuuint32_t box[5] = {(cuuint32_t)W, 256, (cuuint32_t)(M / 256), 1, 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = fn(&A->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, (void*)A->X, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cols_split(lsfft_grid* g, PassArgs<float>* A) {
+    const int M = (int)(g->n[1] / 2);
+    Geom geo;
+    split_col_dispatch(g->logn[1] - 1, OP_QUERY, nullptr, nullptr, &geo);
+    A->n_inner = g->n[0] / 2 + 1;
+    A->Nh = (int64_t)M * A->hp;
+    A->line_axis = 1;
+    A->mode = MODE_COL_GAMMA;
+    const int64_t items = 2 * ((A->n_inner + geo.per_block - 1) / geo.per_block);
+    A->grid_blocks = (int)persistent_blocks(g, items, geo.blocks_per_sm);
+    cudaError_t e = encode_split_map(A, M, geo.per_block);
+    if (e != cudaSuccess) return e;
+    return split_col_dispatch(g->logn[1] - 1, OP_LAUNCH, A, g->stream, nullptr);
+}
+
 template <typename T>
 cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
     Geom geo;
@@ -663,6 +727,9 @@ cudaError_t col_launch(lsfft_grid* g, int axis, PassArgs<T>* A) {
 template <typename T>
 cudaError_t launch_cols(lsfft_grid* g, int st) {
     PassArgs<T> A = base_args<T>(g, st);
+    if constexpr (sizeof(T) == 4) {
+        if (g->split) return launch_cols_split(g, &A);
+    }
     if (g->d == 2) {
         A.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[1] : nullptr;
         A.ls = g->n[0];
@@ -703,11 +770,12 @@ cudaError_t launch_cols(lsfft_grid* g, int st) {
     return col_launch<T>(g, 1, &Y);
 }
 
+// One update: the row pass (whose last block also runs the finalize step: sums,
+// sigma_k, stop rule) and the strided pass(es).
 template <typename T>
 cudaError_t launch_iteration(lsfft_grid* g, int st, int nblocks, int row_mode) {
+    (void)nblocks;
     cudaError_t e = launch_row<T>(g, st, row_mode, nullptr);
-    if (e != cudaSuccess) return e;
-    e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 0, g->stream);
     if (e != cudaSuccess) return e;
     return launch_cols<T>(g, st);
 }
@@ -835,7 +903,7 @@ int begin_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     // guards against kernels that silently did not run.
     g->cur_max_launches = (int64_t)o->max_iter / o->check_every + 2;
     g->cur_launches = 0;
-    g->cur_per_iter = g->d == 2 ? 3 : 5;      // row pass, finalize, strided pass(es)
+    g->cur_per_iter = g->d == 2 ? 2 : 4;      // row pass (finalize in its last block), strided pass(es)
     g->cur_kernels = 2 + g->cur_per_iter;     // init + first update + control block readback
     g->cur_check_every = o->check_every;
     g->cur_st = st;
@@ -881,7 +949,7 @@ int poll_solve(lsfft_grid* g) {
         cudaEventElapsedTime(&ms, g->ev0, g->ev1);
         res->solve_ms = ms;
         res->kernel_launches = g->cur_kernels;
-        res->packed = g->packed;
+        res->packed = g->packed ? (g->split ? 2 : 1) : 0;
         const int L = res->hist_len;
         res->hist_sigma_re = (double*)malloc(sizeof(double) * L);
         res->hist_sigma_im = (double*)malloc(sizeof(double) * L);
@@ -900,12 +968,10 @@ int poll_solve(lsfft_grid* g) {
     }
     if (g->ctrl_host->done) {
         // output pass: E of the last iterate, its sigma_* and averages, history
-        g->cur_kernels += 4;   // output row pass, finalize, two readbacks
+        g->cur_kernels += 3;   // output row pass (with the final averages), two readbacks
         const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
         CK(big_alloc(&g->cur_E, ebytes, g->stream));
         CK(launch_row<T>(g, g->cur_st, MODE_ROW_OUTPUT, (cx<T>*)g->cur_E));
-        CK(launch_finalize(g->partials, g->cur_nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1,
-                           g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
         CK(launch_copy_words(g->ctrl_host_dev, g->ctrl_dev, sizeof(Ctrl), g->stream));
         const int L = g->ctrl_host->iter + 1;
@@ -1057,6 +1123,7 @@ int check_and_setup(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsf
     const int st = o->scheme == LSFFT_EM_SUB ? 2 : (o->scheme == LSFFT_MS_SUB ? 1 : 0);
     *st_out = st;
     g->packed = packed_layout(g, *g->prm_host) ? 1 : 0;
+    g->split = (g->packed && o->precision == LSFFT_FP32 && split_shape(g) && !g->no_split) ? 1 : 0;
     g->bench_prec = -1;
     return ensure_workspace(g, o->precision, st, o->max_iter);
 }
@@ -1135,10 +1202,10 @@ int lsfft_launch_passes(lsfft_grid* g, int kind, int count) {
     for (int i = 0; i < count; ++i) {
         cudaError_t e = cudaSuccess;
         if (g->bench_prec == LSFFT_FP32) {
-            if (kind != 1) e = launch_row<float>(g, g->bench_st, MODE_ROW_ITER, nullptr);
+            if (kind != 1) e = launch_row<float>(g, g->bench_st, MODE_ROW_ITER, nullptr, true);
             if (e == cudaSuccess && kind != 0) e = launch_cols<float>(g, g->bench_st);
         } else {
-            if (kind != 1) e = launch_row<double>(g, g->bench_st, MODE_ROW_ITER, nullptr);
+            if (kind != 1) e = launch_row<double>(g, g->bench_st, MODE_ROW_ITER, nullptr, true);
             if (e == cudaSuccess && kind != 0) e = launch_cols<double>(g, g->bench_st);
         }
         if (e != cudaSuccess) return fail_cuda(e, "lsfft_launch_passes");
@@ -1356,6 +1423,7 @@ int lsfft_lanczos_hull(lsfft_grid* g, const double* e, int green, int precision,
     for (int c = 0; c < g->d; ++c) P->e[c] = e[c];
     P->g_b[0] = 1.0;
     g->packed = 0;
+    g->split = 0;
     g->bench_prec = -1;
     int rc = ensure_workspace(g, precision, 0, 1);
     if (rc != LSFFT_OK) return rc;
@@ -1390,6 +1458,64 @@ int lsfft_lanczos_hull(lsfft_grid* g, const double* e, int green, int precision,
         if (nodes) nodes[i] = th[i];
         if (weights) weights[i] = w2[i];
     }
+    return LSFFT_OK;
+}
+
+int lsfft_set_column_split(lsfft_grid* g, int split) {
+    if (!g) {
+        g_last_error = "lsfft_set_column_split: null grid";
+        return LSFFT_EINVAL;
+    }
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    clear_graphs(g);
+    g->no_split = split == 0;
+    g->bench_prec = -1;
+    return LSFFT_OK;
+}
+
+int lsfft_autotune(lsfft_grid* g, lsfft_c128 sigma1, const double* e, const lsfft_opts* opts, int iters,
+                   lsfft_tuning* out) {
+    if (!g || !e || !opts || !out || iters < 1 || iters > 100000) {
+        g_last_error = "lsfft_autotune: bad arguments";
+        return LSFFT_EINVAL;
+    }
+    const bool both_layouts = split_shape(g) && opts->precision == LSFFT_FP32;
+    const bool saved_no_split = g->no_split;
+    const int ces[] = {4, 8, 16, 32, 64};
+    double best = INFINITY;
+    int best_ce = opts->check_every, best_split = saved_no_split ? 0 : 1, count = 0;
+    for (int split = 1; split >= 0; --split) {
+        if (!both_layouts && split == 0) break;
+        lsfft_set_column_split(g, split);
+        for (int ce : ces) {
+            lsfft_opts o = *opts;
+            o.check_every = ce;
+            o.tol = 0.0;
+            o.max_iter = iters;
+            double ms = INFINITY;
+            for (int rep = 0; rep < 2; ++rep) {   // the first run captures the graph
+                lsfft_result* r = nullptr;
+                const int rc = lsfft_solve(g, sigma1, e, &o, &r);
+                if (!r) {
+                    lsfft_set_column_split(g, saved_no_split ? 0 : 1);
+                    return rc;
+                }
+                if (rep == 1) ms = r->solve_ms / (double)(r->iters > 0 ? r->iters : 1);
+                lsfft_free_result(r);
+            }
+            ++count;
+            if (ms < best) {
+                best = ms;
+                best_ce = ce;
+                best_split = both_layouts ? split : (saved_no_split ? 0 : 1);
+            }
+        }
+    }
+    lsfft_set_column_split(g, best_split);
+    out->check_every = best_ce;
+    out->column_split = best_split;
+    out->ms_per_iter = best;
+    out->candidates = count;
     return LSFFT_OK;
 }
 
@@ -1667,6 +1793,256 @@ int lsfft_effective_tensor(lsfft_grid* g, lsfft_c128 sigma1, const lsfft_opts* o
         release();
     }
     return worst;
+}
+
+int lsfft_solve_sweep(int njobs, const lsfft_job* jobs, lsfft_result** results, int* statuses) {
+    if (njobs < 0 || (njobs > 0 && (!jobs || !results || !statuses))) {
+        g_last_error = "lsfft_solve_sweep: bad arguments";
+        return LSFFT_EINVAL;
+    }
+    if (njobs == 0) return LSFFT_OK;
+    auto pow2_in = [](int64_t v) { return v >= 128 && v <= 1024 && (v & (v - 1)) == 0; };
+    for (int j = 0; j < njobs; ++j) {
+        results[j] = nullptr;
+        statuses[j] = LSFFT_EINVAL;
+        const lsfft_job& J = jobs[j];
+        lsfft_grid* g = J.grid;
+        if (!g || g->d != 2 || !pow2_in(g->n[0]) || !pow2_in(g->n[1]) || g->sigma64 ||
+            J.opts.precision != LSFFT_FP32 || J.opts.max_iter < 1 || J.opts.stop_consecutive < 1 ||
+            !(J.opts.tol >= 0.0) || J.opts.scheme < 0 || J.opts.scheme > 3 || (J.opts.green != 0 && J.opts.green != 1)) {
+            g_last_error = "lsfft_solve_sweep: every job needs a 2-D grid with n_x, n_y in {128, ..., 1024}, "
+                           "a two-phase medium, FP32 fields and valid options";
+            return LSFFT_EINVAL;
+        }
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static int bps_dev[64] = {0};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 0 || dev >= 64) return fail_cuda(cudaErrorInvalidDevice, "lsfft_solve_sweep");
+        if (!bps_dev[dev]) CK(sweep_prepare(&bps_dev[dev]));
+    }
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // descriptors (FP64 constants per job, as lsfft_solve would form them)
+    std::vector<SweepJob> hj((size_t)njobs);
+    std::vector<SchemeParams> prm((size_t)njobs);
+    std::vector<int> hist_off((size_t)njobs), part_off((size_t)njobs);
+    int64_t hist_total = 0, part_total = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const lsfft_job& J = jobs[j];
+        lsfft_grid* g = J.grid;
+        std::string why = build_params(g, cplx(J.sigma1.re, J.sigma1.im), J.e, &J.opts, &prm[j]);
+        if (!why.empty()) {
+            g_last_error = "lsfft_solve_sweep: job " + std::to_string(j) + ": " + why;
+            return LSFFT_EINVAL;
+        }
+        SweepJob& D = hj[j];
+        memset(&D, 0, sizeof(D));
+        D.k = make_kconst<float>(prm[j]);
+        D.prm = prm[j];
+        D.nx = (int)g->n[0];
+        D.ny = (int)g->n[1];
+        D.lognx = g->logn[0];
+        D.logny = g->logn[1];
+        D.row_items = D.ny / sweep_row_lpb(D.nx);
+        D.col_items = D.nx / sweep_col_cols(D.ny);
+        D.mask = g->mask;
+        D.fd[0] = (const float2*)g->fd[0][0];
+        D.fd[1] = (const float2*)g->fd[1][0];
+        hist_off[j] = (int)hist_total;
+        hist_total += (int64_t)(J.opts.max_iter + 1) * HIST_STRIDE;
+        part_off[j] = (int)part_total;
+        part_total += (int64_t)D.row_items * 9;
+    }
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    std::vector<void*> owned;   // buffers freed at the end (the fields E stay with the results)
+    std::vector<void*> fields((size_t)njobs, nullptr);
+    SweepJob* djobs = nullptr;
+    SweepJob* pinned = nullptr;
+    SweepGlobal* dglob = nullptr;
+    SweepGlobal* hglob = nullptr;
+    double* dhist = nullptr;
+    double* dpart = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&](bool keep_fields) {
+        if (s) cudaStreamSynchronize(s);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* p : owned) big_free(p);
+        if (!keep_fields)
+            for (void* p : fields) big_free(p);
+        cudaFree(djobs);
+        cudaFree(dglob);
+        cudaFree(dhist);
+        cudaFree(dpart);
+        if (pinned) cudaFreeHost(pinned);
+        if (hglob) cudaFreeHost(hglob);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s) cudaStreamDestroy(s);
+    };
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < njobs && e == cudaSuccess; ++j) {
+        SweepJob& D = hj[j];
+        const size_t fb = (size_t)2 * D.nx * D.ny * sizeof(float2);
+        const int st = jobs[j].opts.scheme == LSFFT_EM_SUB ? 2 : (jobs[j].opts.scheme == LSFFT_MS_SUB ? 1 : 0);
+        void* p = nullptr;
+        if ((e = big_alloc(&p, fb, s)) != cudaSuccess) break;
+        owned.push_back(p);
+        D.X = (float2*)p;
+        if (st >= 1) {
+            if ((e = big_alloc(&p, fb, s)) != cudaSuccess) break;
+            owned.push_back(p);
+            D.S = (float2*)p;
+        }
+        if (st >= 2) {
+            if ((e = big_alloc(&p, fb, s)) != cudaSuccess) break;
+            owned.push_back(p);
+            D.T = (float2*)p;
+        }
+        if ((e = big_alloc(&p, fb, s)) != cudaSuccess) break;
+        fields[j] = p;
+        D.Eout = (float2*)p;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&djobs, sizeof(SweepJob) * njobs);
+    if (e == cudaSuccess) e = cudaMalloc(&dglob, sizeof(SweepGlobal));
+    if (e == cudaSuccess) e = cudaMalloc(&dhist, sizeof(double) * hist_total);
+    if (e == cudaSuccess) e = cudaMalloc(&dpart, sizeof(double) * part_total);
+    if (e == cudaSuccess) e = cudaMallocHost(&pinned, sizeof(SweepJob) * njobs);
+    if (e == cudaSuccess) e = cudaMallocHost(&hglob, sizeof(SweepGlobal));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup(false);
+        return fail_cuda(e, "lsfft_solve_sweep buffers");
+    }
+    for (int j = 0; j < njobs; ++j) {
+        hj[j].hist = dhist + hist_off[j];
+        hj[j].partials = dpart + part_off[j];
+    }
+    memcpy(pinned, hj.data(), sizeof(SweepJob) * njobs);
+    // the batch as one captured graph: descriptors in, counters cleared, the one
+    // persistent launch, descriptors and counters back
+    const int blocks = sms * std::max(1, bps_dev[dev]);
+    const long long idle_limit_ns = 2000000000LL;
+    const char* step = "cudaStreamBeginCapture";
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaMemcpyAsync(djobs, pinned, sizeof(SweepJob) * njobs, cudaMemcpyHostToDevice, s);
+        const char* lstep = "descriptor upload";
+        if (le == cudaSuccess && (le = cudaMemsetAsync(dglob, 0, sizeof(SweepGlobal), s)) != cudaSuccess)
+            lstep = "counter reset";
+        if (le == cudaSuccess && (le = sweep_launch(djobs, njobs, dglob, blocks, idle_limit_ns, s)) != cudaSuccess)
+            lstep = "persistent launch";
+        if (le == cudaSuccess &&
+            (le = cudaMemcpyAsync(pinned, djobs, sizeof(SweepJob) * njobs, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            lstep = "descriptor readback";
+        if (le == cudaSuccess &&
+            (le = cudaMemcpyAsync(hglob, dglob, sizeof(SweepGlobal), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            lstep = "counter readback";
+        step = "cudaStreamEndCapture";
+        e = cudaStreamEndCapture(s, &graph);
+        if (e == cudaSuccess && le != cudaSuccess) {
+            e = le;
+            step = lstep;
+        }
+    }
+    if (e == cudaSuccess) {
+        step = "cudaGraphInstantiate";
+        e = cudaGraphInstantiate(&exec, graph, 0);
+    }
+    if (e == cudaSuccess) {
+        // timing events outside the captured graph (an event recorded during capture
+        // is not recorded when the graph runs)
+        step = "cudaGraphLaunch";
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    }
+    if (e == cudaSuccess) {
+        step = "the persistent launch (cudaStreamSynchronize)";
+        e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        cleanup(false);
+        return fail_cuda(e, (std::string("lsfft_solve_sweep: ") + step).c_str());
+    }
+    if (hglob->error || hglob->jobs_done != njobs) {
+        cleanup(false);
+        g_last_error = "lsfft_solve_sweep: the persistent launch stopped early (a block found no work for two "
+                       "seconds while solves remained)";
+        return LSFFT_ECUDA;
+    }
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+        cleanup(false);
+        return fail_cuda(e, "lsfft_solve_sweep: elapsed time");
+    }
+    std::vector<double> hh((size_t)hist_total);
+    e = cudaMemcpy(hh.data(), dhist, sizeof(double) * hist_total, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cleanup(false);
+        return fail_cuda(e, "lsfft_solve_sweep history");
+    }
+    for (int j = 0; j < njobs; ++j) {
+        const SweepJob& D = pinned[j];
+        const lsfft_job& J = jobs[j];
+        lsfft_result* res = (lsfft_result*)calloc(1, sizeof(lsfft_result));
+        if (!res) {
+            statuses[j] = LSFFT_ENOMEM;
+            continue;
+        }
+        res->precision = LSFFT_FP32;
+        res->sigma1 = J.sigma1;
+        res->d = 2;
+        res->n[0] = D.nx;
+        res->n[1] = D.ny;
+        res->n[2] = 1;
+        res->iters = D.ctrl.iter;
+        res->status = D.ctrl.status;
+        res->sigma_star.re = D.ctrl.sigma[0];
+        res->sigma_star.im = D.ctrl.sigma[1];
+        for (int c = 0; c < 2; ++c) {
+            res->mean_E[c].re = D.ctrl.meanE[c][0];
+            res->mean_E[c].im = D.ctrl.meanE[c][1];
+            res->mean_J[c].re = D.ctrl.meanJ[c][0];
+            res->mean_J[c].im = D.ctrl.meanJ[c][1];
+        }
+        res->solve_ms = ms;             // the whole batch's device time
+        res->kernel_launches = 1;       // the one persistent launch, shared by every job
+        res->packed = 0;
+        const int L = D.ctrl.iter + 1;
+        res->hist_len = L;
+        res->hist_sigma_re = (double*)malloc(sizeof(double) * L);
+        res->hist_sigma_im = (double*)malloc(sizeof(double) * L);
+        res->hist_rel_change = (double*)malloc(sizeof(double) * L);
+        res->hist_field_norm = (double*)malloc(sizeof(double) * L);
+        if (!res->hist_sigma_re || !res->hist_sigma_im || !res->hist_rel_change || !res->hist_field_norm) {
+            lsfft_free_result(res);
+            statuses[j] = LSFFT_ENOMEM;
+            continue;
+        }
+        const double* h = hh.data() + hist_off[j];
+        for (int k = 0; k < L; ++k) {
+            res->hist_sigma_re[k] = h[HIST_STRIDE * k + 0];
+            res->hist_sigma_im[k] = h[HIST_STRIDE * k + 1];
+            res->hist_rel_change[k] = h[HIST_STRIDE * k + 2];
+            res->hist_field_norm[k] = h[HIST_STRIDE * k + 3];
+        }
+        res->E_device = fields[j];
+        fields[j] = nullptr;
+        results[j] = res;
+        statuses[j] = res->status == ST_OK ? LSFFT_OK : res->status;
+    }
+    cleanup(false);   // fields handed to results are no longer in `fields`
+    return LSFFT_OK;
 }
 
 int lsfft_substitution_rates(lsfft_c128 sigma1, double alpha, double beta, double* rate, double* limit) {

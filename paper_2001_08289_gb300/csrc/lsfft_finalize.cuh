@@ -1,0 +1,128 @@
+// Scalar recurrence of one iteration (FP64, one thread): sigma_k of Eq. J13
+// projected on e from the volume sums, the relative changes of sigma_k and of
+// <|E|^2>, the history entry, and the stop rule (K consecutive changes below
+// tol, divergence, iteration cap).  tot[4c + 0..3] = sums of Re, Im E_c and
+// Re, Im J_c; tot[4d] = sum of |E|^2 (all over the N voxels).  final_mode: the
+// output pass of a finished solve (history and averages only).
+#pragma once
+
+#include <math.h>
+
+#include "lsfft_params.h"
+
+namespace lsfft {
+
+__device__ __forceinline__ void finalize_update(const double* tot, const SchemeParams& P, Ctrl* ctrl, double* hist,
+                                                int final_mode) {
+    const int d = P.d;
+    // sigma_k = (<J>.e) / (<E>.e); the 1/N factors cancel
+    double je_re = 0, je_im = 0, ee_re = 0, ee_im = 0;
+    for (int c = 0; c < d; ++c) {
+        ee_re += tot[4 * c + 0] * P.e[c];
+        ee_im += tot[4 * c + 1] * P.e[c];
+        je_re += tot[4 * c + 2] * P.e[c];
+        je_im += tot[4 * c + 3] * P.e[c];
+    }
+    const double den = ee_re * ee_re + ee_im * ee_im;
+    const double s_re = (je_re * ee_re + je_im * ee_im) / den;
+    const double s_im = (je_im * ee_re - je_re * ee_im) / den;
+    const double norm = tot[4 * d] * P.inv_ntot;
+    const int k = ctrl->iter;
+    const double mag = sqrt(s_re * s_re + s_im * s_im);
+    double rel = INFINITY;
+    if (k >= 1 && mag != 0.0) {
+        const double dr = s_re - ctrl->prev[0], di = s_im - ctrl->prev[1];
+        rel = sqrt(dr * dr + di * di) / mag;
+    }
+    hist[(int64_t)k * HIST_STRIDE + 0] = s_re;
+    hist[(int64_t)k * HIST_STRIDE + 1] = s_im;
+    hist[(int64_t)k * HIST_STRIDE + 2] = rel;
+    hist[(int64_t)k * HIST_STRIDE + 3] = norm;
+    ctrl->sigma[0] = s_re;
+    ctrl->sigma[1] = s_im;
+    for (int c = 0; c < d; ++c) {
+        ctrl->meanE[c][0] = tot[4 * c + 0] * P.inv_ntot;
+        ctrl->meanE[c][1] = tot[4 * c + 1] * P.inv_ntot;
+        ctrl->meanJ[c][0] = tot[4 * c + 2] * P.inv_ntot;
+        ctrl->meanJ[c][1] = tot[4 * c + 3] * P.inv_ntot;
+    }
+    // relative change of <|E|^2>: the field must settle as well as sigma_*
+    const double nrel = (k >= 1 && norm != 0.0) ? fabs(norm - ctrl->prev_norm) / norm : INFINITY;
+    ctrl->prev[0] = s_re;
+    ctrl->prev[1] = s_im;
+    ctrl->prev_norm = norm;
+    if (final_mode) return;
+    if (k == 0) ctrl->norm0 = norm;
+    ctrl->run = (rel < P.tol && nrel < P.tol) ? ctrl->run + 1 : 0;
+    const bool diverged = !isfinite(s_re) || !isfinite(s_im) || !isfinite(norm) ||
+                          norm > DIVERGENCE_FACTOR * ctrl->norm0;
+    if (diverged) {
+        ctrl->status = ST_DIVERGED;
+        ctrl->done = 1;
+    } else if (ctrl->run >= P.consecutive) {
+        ctrl->status = ST_OK;
+        ctrl->done = 1;
+    } else if (k + 1 >= P.max_iter) {
+        ctrl->status = ST_NOTCONV;
+        ctrl->done = 1;
+    }
+    ctrl->iter = k + 1;
+}
+
+// The finalize step fused into a pass: every block has written its partial sums
+// partials[blockIdx][0..NV); each then counts itself in ctrl->arrivals, and the
+// block that arrives last (all partials are then visible) sums them over the
+// blocks in a fixed order (blocks strided over the threads, a shuffle tree, the
+// warps in order), runs the scalar recurrence and resets the count for the next
+// launch.  Call from every thread of every block, after the partials are written.
+template <int NV, int NT>
+__device__ __forceinline__ void finalize_last_block(const double* partials, const SchemeParams& P, Ctrl* ctrl,
+                                                    double* hist, int final_mode) {
+    __shared__ double tot[NV];
+    __shared__ double red[NT / 32 > 0 ? NT / 32 : 1][NV];
+    __shared__ int last;
+    __threadfence();   // publish this block's partials
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctrl->arrivals, 1u) + 1 == gridDim.x;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();   // acquire: the other blocks' partials, read through L2
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double x[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += NT)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) x[v] += __ldcg(partials + (int64_t)b * NV + v);
+    if constexpr (NT >= 32) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            for (int o = 16; o > 0; o >>= 1) x[v] += __shfl_down_sync(0xffffffffu, x[v], o);
+            if (lane == 0) red[warp][v] = x[v];
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
+            tot[threadIdx.x] = s;
+        }
+    } else {   // a block narrower than a warp: thread 0 adds the threads' sums in order
+#pragma unroll
+        for (int v = 0; v < NV; ++v) red[0][v] = 0.0;
+        __syncthreads();
+        for (int i = 0; i < NT; ++i) {
+            if (threadIdx.x == i)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) red[0][v] += x[v];
+            __syncthreads();
+        }
+        if (threadIdx.x < NV) tot[threadIdx.x] = red[0][threadIdx.x];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        finalize_update(tot, P, ctrl, hist, final_mode);
+        ctrl->arrivals = 0;
+    }
+}
+
+}  // namespace lsfft

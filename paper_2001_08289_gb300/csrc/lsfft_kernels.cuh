@@ -31,6 +31,7 @@
 #include <cuda.h>   // CUtensorMap (the encoding itself goes through the runtime's driver entry point)
 
 #include "lsfft_fft.cuh"
+#include "lsfft_finalize.cuh"
 #include "lsfft_params.h"
 #include "lsfft_tma.cuh"
 
@@ -448,6 +449,10 @@ struct PassArgs {
     int grid_blocks;          // persistent grid size chosen by the host
     int packed;               // packed real layout (2-D row pass only; the strided pass sees two planes)
     KConst<T> k;
+    SchemeParams prm;         // FP64 constants of the scalar recurrence (fused finalize)
+    double* hist;             // history of the solve (fused finalize)
+    int fuse_fin;             // row pass: the last block runs the finalize step (2: sums and history
+                              // only, without the stop rule: pass timing of lsfft_launch_passes)
     long long wait_limit;     // bound of every mbarrier wait, in clock cycles
     int extra_tx;             // test hook: bytes announced but never delivered (0 in normal runs)
     CUtensorMap tmap;         // strided passes: TMA view of the planes (encoded by the host)
@@ -465,7 +470,12 @@ row_pass(const PassArgs<T> A) {
     constexpr int PS = Cfg::P::S, PX = Cfg::P::X;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int mode = A.mode;
-    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;
+    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) {
+        // the solve has stopped: with the finalize fused here, this pass also tells the
+        // strided passes of the launch to skip
+        if (A.fuse_fin && blockIdx.x == 0 && threadIdx.x == 0) A.ctrl->skipB = 1;
+        return;
+    }
 
     C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][LPB][PS]
     const int g = threadIdx.x / TL, t = threadIdx.x % TL;
@@ -783,6 +793,9 @@ row_pass(const PassArgs<T> A) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) dacc[i] = (double)acc[i] - (double)cmp[i];
     block_reduce_store<NV, Cfg::THREADS>(dacc, A.partials + (int64_t)blockIdx.x * NV);
+    if (A.fuse_fin)
+        finalize_last_block<NV, Cfg::THREADS>(A.partials, A.prm, A.ctrl, A.hist,
+                                              mode == MODE_ROW_OUTPUT || A.fuse_fin == 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -792,9 +805,9 @@ row_pass(const PassArgs<T> A) {
 // index; FD: Gamma(k) = u u^H/|u|^2 with u_a = exp(2 pi i k_a/n_a) - 1.
 // ---------------------------------------------------------------------------
 template <typename T, int D>
-__device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], const PassArgs<T>& A) {
+__device__ __forceinline__ void gamma_apply_k(cx<T> (&v)[D], const int (&ki)[3], const KConst<T>& K, const int* nn,
+                                              const cx<T>* const* fd) {
     using C = cx<T>;
-    const KConst<T>& K = A.k;
     bool zero = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) zero = zero && (ki[a] == 0);
@@ -808,14 +821,14 @@ __device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], c
     if (K.green == GREEN_TRIG) {
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const int n = A.n[a];
+            const int n = nn[a];
             const int k = ki[a] < n / 2 ? ki[a] : ki[a] - n;
             nyq = nyq || (ki[a] == n / 2);
             u[a] = mkc((T)k, (T)0);
         }
     } else {
 #pragma unroll
-        for (int a = 0; a < D; ++a) u[a] = A.fd[a][ki[a]];
+        for (int a = 0; a < D; ++a) u[a] = fd[a][ki[a]];
     }
     if (nyq) {
 #pragma unroll
@@ -832,6 +845,11 @@ __device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], c
     const C proj = cscale(cmul(K.g_b, dot), (T)1 / nrm);
 #pragma unroll
     for (int c = 0; c < D; ++c) v[c] = cadd(cmul(K.g_a, v[c]), cmul(proj, u[c]));
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void gamma_apply(cx<T> (&v)[D], const int (&ki)[3], const PassArgs<T>& A) {
+    gamma_apply_k<T, D>(v, ki, A.k, A.n, A.fd);
 }
 
 // ---------------------------------------------------------------------------

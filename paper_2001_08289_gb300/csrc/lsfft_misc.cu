@@ -1,7 +1,9 @@
-// Small kernels around the passes: initial state and the FP64 finalize step
-// (volume averages, sigma_k of Eq. J13, stop rule).
+// Small kernels around the passes: initial state, small device-to-host
+// transfers, Lanczos vector operations and the gradient.  (The FP64 finalize
+// step runs in the last block of each row pass: lsfft_finalize.cuh.)
 #include <math.h>
 
+#include "lsfft_finalize.cuh"
 #include "lsfft_misc.h"
 
 namespace lsfft {
@@ -38,102 +40,6 @@ __global__ void init_state_kernel(cx<T>* __restrict__ X, cx<T>* __restrict__ S, 
     }
 }
 
-// One block of FIN_THREADS threads.  Sums partials[b][v] over blocks in a fixed
-// order (deterministic), then thread 0 updates the scalar recurrence.
-constexpr int FIN_THREADS = 256;
-
-__global__ void __launch_bounds__(FIN_THREADS)
-finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const SchemeParams P,
-                Ctrl* __restrict__ ctrl, double* __restrict__ hist, int final_mode) {
-    constexpr int NVMAX = 16;   // nv = 4 d + 1 <= 13
-    __shared__ double tot[NVMAX];
-    __shared__ double red[FIN_THREADS / 32][NVMAX];
-    if (!final_mode && ctrl->done) {
-        if (threadIdx.x == 0) ctrl->skipB = 1;
-        return;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // every value at once (its loads in flight together), each in the same
-    // fixed order: blocks strided over the threads, a shuffle tree, the warps
-    double x[NVMAX];
-#pragma unroll
-    for (int v = 0; v < NVMAX; ++v) x[v] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += FIN_THREADS) {
-        const double* pb = partials + (int64_t)b * nv;
-#pragma unroll
-        for (int v = 0; v < NVMAX; ++v)
-            if (v < nv) x[v] += pb[v];
-    }
-#pragma unroll
-    for (int v = 0; v < NVMAX; ++v) {
-        if (v < nv) {
-            for (int o = 16; o > 0; o >>= 1) x[v] += __shfl_down_sync(0xffffffffu, x[v], o);
-            if (lane == 0) red[warp][v] = x[v];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < nv) {
-        double s = 0.0;
-        for (int w = 0; w < FIN_THREADS / 32; ++w) s += red[w][threadIdx.x];
-        tot[threadIdx.x] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    const int d = P.d;
-    // sigma_k = (<J>.e) / (<E>.e); the 1/N factors cancel
-    double je_re = 0, je_im = 0, ee_re = 0, ee_im = 0;
-    for (int c = 0; c < d; ++c) {
-        ee_re += tot[4 * c + 0] * P.e[c];
-        ee_im += tot[4 * c + 1] * P.e[c];
-        je_re += tot[4 * c + 2] * P.e[c];
-        je_im += tot[4 * c + 3] * P.e[c];
-    }
-    const double den = ee_re * ee_re + ee_im * ee_im;
-    const double s_re = (je_re * ee_re + je_im * ee_im) / den;
-    const double s_im = (je_im * ee_re - je_re * ee_im) / den;
-    const double norm = tot[4 * d] * P.inv_ntot;
-    const int k = ctrl->iter;
-    const double mag = sqrt(s_re * s_re + s_im * s_im);
-    double rel = INFINITY;
-    if (k >= 1 && mag != 0.0) {
-        const double dr = s_re - ctrl->prev[0], di = s_im - ctrl->prev[1];
-        rel = sqrt(dr * dr + di * di) / mag;
-    }
-    hist[(int64_t)k * HIST_STRIDE + 0] = s_re;
-    hist[(int64_t)k * HIST_STRIDE + 1] = s_im;
-    hist[(int64_t)k * HIST_STRIDE + 2] = rel;
-    hist[(int64_t)k * HIST_STRIDE + 3] = norm;
-    ctrl->sigma[0] = s_re;
-    ctrl->sigma[1] = s_im;
-    for (int c = 0; c < d; ++c) {
-        ctrl->meanE[c][0] = tot[4 * c + 0] * P.inv_ntot;
-        ctrl->meanE[c][1] = tot[4 * c + 1] * P.inv_ntot;
-        ctrl->meanJ[c][0] = tot[4 * c + 2] * P.inv_ntot;
-        ctrl->meanJ[c][1] = tot[4 * c + 3] * P.inv_ntot;
-    }
-    // relative change of <|E|^2>: the field must settle as well as sigma_*
-    const double nrel = (k >= 1 && norm != 0.0) ? fabs(norm - ctrl->prev_norm) / norm : INFINITY;
-    ctrl->prev[0] = s_re;
-    ctrl->prev[1] = s_im;
-    ctrl->prev_norm = norm;
-    if (final_mode) return;
-    if (k == 0) ctrl->norm0 = norm;
-    ctrl->run = (rel < P.tol && nrel < P.tol) ? ctrl->run + 1 : 0;
-    const bool diverged = !isfinite(s_re) || !isfinite(s_im) || !isfinite(norm) ||
-                          norm > DIVERGENCE_FACTOR * ctrl->norm0;
-    if (diverged) {
-        ctrl->status = ST_DIVERGED;
-        ctrl->done = 1;
-    } else if (ctrl->run >= P.consecutive) {
-        ctrl->status = ST_OK;
-        ctrl->done = 1;
-    } else if (k + 1 >= P.max_iter) {
-        ctrl->status = ST_NOTCONV;
-        ctrl->done = 1;
-    }
-    ctrl->iter = k + 1;
-}
-
 template <typename T>
 cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams& prm, int64_t Ntot,
                         int d, int packed, const cx<T>* sigma, int sm_count, cudaStream_t s) {
@@ -141,12 +47,6 @@ cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, cons
     const int64_t cap = (int64_t)sm_count * 8;
     if (blocks > cap) blocks = cap;
     init_state_kernel<T><<<(unsigned)blocks, 256, 0, s>>>(X, S, Tf, mask, prm, Ntot, d, packed, sigma);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
-                            double* hist, int final_mode, cudaStream_t s) {
-    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(partials, nblocks, nv, prm, ctrl, hist, final_mode);
     return cudaGetLastError();
 }
 

@@ -28,9 +28,6 @@ template <typename T>
 cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams& prm, int64_t Ntot,
                         int d, int packed, const cx<T>* sigma, int sm_count, cudaStream_t s);
 
-cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
-                            double* hist, int final_mode, cudaStream_t s);
-
 // Copy `bytes` (a multiple of 8) from device memory to the device view of
 // mapped pinned host memory with one small kernel on stream s.
 cudaError_t launch_copy_words(void* dst, const void* src, size_t bytes, cudaStream_t s);
@@ -51,6 +48,10 @@ template <> cudaError_t col_dispatch<float, 2>(int, int, const PassArgs<float>*,
 template <> cudaError_t col_dispatch<float, 3>(int, int, const PassArgs<float>*, cudaStream_t, Geom*);
 template <> cudaError_t col_dispatch<double, 2>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
 template <> cudaError_t col_dispatch<double, 3>(int, int, const PassArgs<double>*, cudaStream_t, Geom*);
+// Split layout of long 2-D columns, FP32 packed fields (lsfft_inst_split.cu):
+// row pass on row pairs of lines 2^logn, strided pass on columns of 2^logm = n_y / 2.
+cudaError_t split_row_dispatch(int logn, int op, const PassArgs<float>* A, cudaStream_t s, Geom* g);
+cudaError_t split_col_dispatch(int logm, int op, const PassArgs<float>* A, cudaStream_t s, Geom* g);
 }  // namespace lsfft
 
 namespace lsfft {

@@ -50,6 +50,13 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, int c0, int
         "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(src)
         : "memory");
 }
+// Contiguous global -> shared copy by the bulk-copy engine, completing on an
+// mbarrier: both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // at most n (0 or 1) bulk groups may still be reading shared memory
 __device__ __forceinline__ void bulk_wait_read(int n) {
