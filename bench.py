@@ -504,39 +504,56 @@ def _line(metric, value, unit, args, config, **extra):
 
 
 def run_lattice64(args):
-    """64^2 square array, sigma_1 = 10, FP64, stop at relative change 1e-10: microseconds
-    per iteration and iterations per scheme (latency-bound: not a roofline case)."""
+    """Config 1: the 64^2 square array, sigma_1 = 10, FP64, stop at relative change
+    1e-10; MS, EM and both substituted schemes with [alpha, beta] from the oracle's
+    dense pole computation on the same grid (weight cutoffs 1e-10 and 1e-3, both
+    Green symbols; stored in tests/golden/dense_pole_hulls_64.json by a script that
+    calls only the oracle), with the GPU Lanczos hull reported beside them.
+    Microseconds per iteration and iterations per scheme (latency-bound: not a
+    roofline case)."""
     torch, L = _gpu_setup()
     mask = square_array_mask(64)
     e = [1.0, 0.0]
-    out = {}
+    fixture = json.load(open(os.path.join(ROOT, "tests", "golden", "dense_pole_hulls_64.json")))["hulls"]
+    out, lanczos = {}, {}
+
+    def timed(g, **kw):
+        for _ in range(args.warmup):
+            g.solve(10.0, e, **kw).free()
+        ms, its, sig = [], [], None
+        for _ in range(args.steps):
+            r = g.solve(10.0, e, **kw)
+            ms.append(r.solve_ms)
+            its.append(r.iterations)
+            sig = r.sigma_star
+            r.free()
+        return {"iters": its[-1], "solve_ms": round(float(np.median(ms)), 4),
+                "us_per_iter": round(1e3 * float(np.median(ms)) / its[-1], 2), "sigma_star": sig.real}
+
     with L.Grid(mask) as g:
-        hulls = {}
         for green, cut in (("trig", 1e-3), ("fd", 1e-10)):
             a, b, _, _ = g.lanczos_hull(e, green=green, precision="fp64", steps=200, cutoff=cut)
-            hulls[green] = (a, b)
+            lanczos[green] = {"cutoff": cut, "alpha": a, "beta": b}
         for green in ("trig", "fd"):
-            a, b = hulls[green]
-            for sch in ("ms", "em", "ms_sub", "em_sub"):
-                kw = dict(scheme=sch, precision="fp64", green=green, tol=1e-10, max_iter=2000, alpha=a, beta=b)
-                for _ in range(args.warmup):
-                    g.solve(10.0, e, **kw).free()
-                ms, its = [], []
-                for _ in range(args.steps):
-                    r = g.solve(10.0, e, **kw)
-                    ms.append(r.solve_ms)
-                    its.append(r.iterations)
-                    sig = r.sigma_star
-                    r.free()
-                out[f"{green}|{sch}"] = {"iters": its[-1], "solve_ms": round(float(np.median(ms)), 4),
-                                         "us_per_iter": round(1e3 * float(np.median(ms)) / its[-1], 2),
-                                         "sigma_star": sig.real}
+            base = dict(precision="fp64", green=green, tol=1e-10, max_iter=4000)
+            for sch in ("ms", "em"):
+                out[f"{green}|{sch}"] = timed(g, scheme=sch, **base)
+            for cutoff in ("1e-10", "0.001"):
+                h = fixture[f"{green}|{cutoff}"]
+                for sch in ("ms_sub", "em_sub"):
+                    out[f"{green}|{sch}|dense poles {cutoff}"] = timed(g, scheme=sch, alpha=h["alpha"],
+                                                                       beta=h["beta"], **base)
+            for sch in ("ms_sub", "em_sub"):
+                out[f"{green}|{sch}|lanczos"] = timed(g, scheme=sch, alpha=lanczos[green]["alpha"],
+                                                      beta=lanczos[green]["beta"], **base)
     tot_vox = sum(v["iters"] for v in out.values()) * mask.size
     tot_s = sum(v["solve_ms"] for v in out.values()) / 1e3
+    us = sorted(v["us_per_iter"] for v in out.values())
     _line("voxel-iters/s (64^2 FP64 lattice)", tot_vox / tot_s, UNIT, args,
-          {"workload": "64x64 square array, sigma1=10, FP64, stop 1e-10, alpha/beta from GPU Lanczos "
-                       "(trig: cutoff 1e-3, fd: cutoff 1e-10)", "hulls": hulls},
-          dtype="c128", per_scheme=out)
+          {"workload": "64x64 square array, sigma1=10, FP64, stop 1e-10; alpha, beta of the substituted schemes "
+                       "from the oracle's dense poles (cutoffs 1e-10 and 1e-3) and from GPU Lanczos",
+           "dense_pole_hulls": fixture, "lanczos_hulls": lanczos},
+          dtype="c128", per_scheme=out, us_per_iter_median=us[len(us) // 2])
 
 
 def run_cube3d(args):

@@ -199,12 +199,13 @@ int lsfft_effective_tensor(lsfft_grid *grid, lsfft_c128 sigma1, const lsfft_opts
 /* Strided-pass layout of long 2-D columns (the paper has no counterpart; a
  * tuning control).  It applies to 2-D grids with n_x, n_y in {4096, 8192} whose
  * solves run FP32 fields with real coefficients (the packed real layout).
- * split = 1 (default): the row pass works on row pairs (j, j + n_y/2) and applies
- * the first radix-2 step of every y-DFT (decimation in frequency), so the
- * strided pass transforms independent columns of n_y/2 points on one SM each.
- * split = 0: the strided pass transforms whole columns on two-block clusters
- * that exchange half-transforms through distributed shared memory.  Both give
- * the same iterates up to rounding.  Takes effect from the next solve or
+ * split = 1: the row pass works on row pairs (j, j + n_y/2) and applies the
+ * first radix-2 step of every y-DFT (decimation in frequency), so the strided
+ * pass transforms independent columns of n_y/2 points on one SM each.
+ * split = 0 (default, measured faster at 4096^2 and 8192^2 on GB300): the
+ * strided pass transforms whole columns on two-block clusters that exchange
+ * half-transforms through distributed shared memory.  Both give the same
+ * iterates up to rounding; lsfft_autotune measures both.  Takes effect from the next solve or
  * lsfft_prepare; waits for the grid's pending work.  EINVAL for a null grid. */
 int lsfft_set_column_split(lsfft_grid *grid, int split);
 

@@ -147,7 +147,7 @@ struct lsfft_grid {
     bool prepared[2] = {false, false};
     int packed = 0;                 // packed real layout for the current solve
     int split = 0;                  // packed FP32 2-D with n_y >= 4096: split layout (lsfft_split.cuh)
-    bool no_split = false;          // lsfft_set_layout: keep the cluster strided pass instead
+    bool no_split = true;           // lsfft_set_column_split(grid, 1) selects the split layout
     // solve in flight (begin_solve / poll_solve)
     int phase = 0;                  // 0 idle, 1 in flight
     bool phase_finish = false;      // the output pass has been enqueued
@@ -537,6 +537,7 @@ KConst<T> make_kconst(const SchemeParams& P) {
     for (int c = 0; c < 3; ++c) K.e[c] = (T)P.e[c];
     K.scheme = P.scheme;
     K.green = P.green;
+    K.real_coef = (P.g_a[1] == 0.0 && P.g_b[1] == 0.0 && P.g_a0[1] == 0.0 && P.g_ce[1] == 0.0) ? 1 : 0;
     return K;
 }
 
@@ -570,11 +571,6 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
     A.k = make_kconst<T>(*g->prm_host);
     A.ctrl = g->ctrl_dev;
     A.partials = g->partials;
-    A.prm = *g->prm_host;
-    A.hist = g->hist;
-    // the row pass runs the finalize step in its last block, except for the
-    // operator of the pole problem (Lanczos), which has no scalar recurrence
-    A.fuse_fin = g->prm_host->scheme != SCHEME_MATVEC ? 1 : 0;
     for (int a = 0; a < 3; ++a) A.fd[a] = a < g->d ? (const cx<T>*)g->fd[a][p] : nullptr;
     A.wait_limit = g->wait_limit;
     A.extra_tx = g->inject_tx;
@@ -586,9 +582,8 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
 }
 
 template <typename T>
-cudaError_t launch_row(lsfft_grid* g, int st, int mode, cx<T>* Eout, bool timing_only = false) {
+cudaError_t launch_row(lsfft_grid* g, int st, int mode, cx<T>* Eout) {
     PassArgs<T> A = base_args<T>(g, st);
-    if (timing_only && A.fuse_fin) A.fuse_fin = 2;   // repeated passes are no iteration: never stop
     A.Eout = Eout;
     A.tw = sizeof(T) == 8 ? (const cx<T>*)g->tw[0] : nullptr;
     A.n_lines = g->N / g->n[0];
@@ -770,12 +765,13 @@ cudaError_t launch_cols(lsfft_grid* g, int st) {
     return col_launch<T>(g, 1, &Y);
 }
 
-// One update: the row pass (whose last block also runs the finalize step: sums,
-// sigma_k, stop rule) and the strided pass(es).
+// One update: the row pass, the finalize step (sums, sigma_k, stop rule) and
+// the strided pass(es).
 template <typename T>
 cudaError_t launch_iteration(lsfft_grid* g, int st, int nblocks, int row_mode) {
-    (void)nblocks;
     cudaError_t e = launch_row<T>(g, st, row_mode, nullptr);
+    if (e != cudaSuccess) return e;
+    e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 0, g->stream);
     if (e != cudaSuccess) return e;
     return launch_cols<T>(g, st);
 }
@@ -903,7 +899,7 @@ int begin_solve(lsfft_grid* g, const lsfft_opts* o, int st, lsfft_result* res) {
     // guards against kernels that silently did not run.
     g->cur_max_launches = (int64_t)o->max_iter / o->check_every + 2;
     g->cur_launches = 0;
-    g->cur_per_iter = g->d == 2 ? 2 : 4;      // row pass (finalize in its last block), strided pass(es)
+    g->cur_per_iter = g->d == 2 ? 3 : 5;      // row pass, finalize, strided pass(es)
     g->cur_kernels = 2 + g->cur_per_iter;     // init + first update + control block readback
     g->cur_check_every = o->check_every;
     g->cur_st = st;
@@ -968,10 +964,12 @@ int poll_solve(lsfft_grid* g) {
     }
     if (g->ctrl_host->done) {
         // output pass: E of the last iterate, its sigma_* and averages, history
-        g->cur_kernels += 3;   // output row pass (with the final averages), two readbacks
+        g->cur_kernels += 4;   // output row pass, finalize, two readbacks
         const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
         CK(big_alloc(&g->cur_E, ebytes, g->stream));
         CK(launch_row<T>(g, g->cur_st, MODE_ROW_OUTPUT, (cx<T>*)g->cur_E));
+        CK(launch_finalize(g->partials, g->cur_nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1,
+                           g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
         CK(launch_copy_words(g->ctrl_host_dev, g->ctrl_dev, sizeof(Ctrl), g->stream));
         const int L = g->ctrl_host->iter + 1;
@@ -1202,10 +1200,10 @@ int lsfft_launch_passes(lsfft_grid* g, int kind, int count) {
     for (int i = 0; i < count; ++i) {
         cudaError_t e = cudaSuccess;
         if (g->bench_prec == LSFFT_FP32) {
-            if (kind != 1) e = launch_row<float>(g, g->bench_st, MODE_ROW_ITER, nullptr, true);
+            if (kind != 1) e = launch_row<float>(g, g->bench_st, MODE_ROW_ITER, nullptr);
             if (e == cudaSuccess && kind != 0) e = launch_cols<float>(g, g->bench_st);
         } else {
-            if (kind != 1) e = launch_row<double>(g, g->bench_st, MODE_ROW_ITER, nullptr, true);
+            if (kind != 1) e = launch_row<double>(g, g->bench_st, MODE_ROW_ITER, nullptr);
             if (e == cudaSuccess && kind != 0) e = launch_cols<double>(g, g->bench_st);
         }
         if (e != cudaSuccess) return fail_cuda(e, "lsfft_launch_passes");

@@ -19,17 +19,10 @@
 // Twiddles: FP32 uses sincospif() for W^{(j mod NS)} once per butterfly and
 // forms the other powers as products of W^{jm}, W^{2jm}, W^{4jm}, W^{8jm};
 // FP64 reads them from a table W_L^k built on the host in double precision.
-// With TWT (FP32, one radix-R butterfly per thread and stage), the factors of
-// every such stage depend on the thread's position only: init_twiddles()
-// computes them once per launch, each by its own sincospif, into the thread's
-// row of tensor memory (32 columns per stage), and each stage loads its R - 1
-// factors with one tcgen05.ld instead of forming them.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
-
-#include "lsfft_tmem.cuh"
 
 namespace lsfft {
 
@@ -191,49 +184,11 @@ __device__ __forceinline__ void line_sync() {
 
 // SMS: element stride of the exchange line in shared memory (SMS lines
 // interleaved position by position share one buffer).
-template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false, int SYNC = 0, int SMS = 1,
-          bool TWT = false>
+template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false, int SYNC = 0, int SMS = 1>
 struct LineFFT {
     using C = cx<T>;
     static constexpr int TL = N / E;   // threads per line
     static_assert(N % E == 0, "E must divide N");
-
-    // Stage NS keeps its factors in tensor memory: FP32, one radix-16 butterfly
-    // per thread (R = E = 16), not the first stage.  Slot = index of the stage
-    // among those, 32 columns each.
-    template <int NS>
-    __host__ __device__ static constexpr bool tw_in_tmem() {
-        constexpr int R = N / NS >= RMAX ? RMAX : N / NS;
-        return TWT && sizeof(T) == 4 && NS > 1 && R == 16 && E == 16;
-    }
-    template <int NS>
-    __host__ __device__ static constexpr int tw_slot() { return ilog2c(NS) / 4 - 1; }
-    __host__ __device__ static constexpr int tw_slots() { return TWT ? (ilog2c(N) - 1) / 4 : 0; }
-
-    // Forward factors W_{NS R}^{(t mod NS) r}, r = 1..15, of every TMEM stage into
-    // the thread's columns at twa (call from every thread of the line's warps,
-    // convergently; the caller waits with tmem_wait_st before the first run()).
-    template <int NS = 1>
-    __device__ __forceinline__ static void init_twiddles(int t, uint32_t twa) {
-        if constexpr (NS < N) {
-            constexpr int R = N / NS >= RMAX ? RMAX : N / NS;
-            if constexpr (tw_in_tmem<NS>()) {
-                float tr[32];
-                const int jm = t % NS;
-#pragma unroll
-                for (int r = 1; r < 16; ++r) {
-                    float sn, cs;
-                    // exact integer product, reduced modulo the period before the division
-                    sincospif(2.0f * (float)((jm * r) % (NS * R)) / (float)(NS * R), &sn, &cs);
-                    tr[2 * (r - 1)] = cs;
-                    tr[2 * (r - 1) + 1] = -sn;
-                }
-                tr[30] = tr[31] = 0.0f;
-                tmem_st32(twa + 32 * tw_slot<NS>(), tr);
-            }
-            init_twiddles<NS * R>(t, twa);
-        }
-    }
 
     template <int R>
     __device__ __forceinline__ static void twiddle(C (&a)[R], int jm, int span, const C* __restrict__ tw,
@@ -281,7 +236,7 @@ struct LineFFT {
 
     template <int NS>
     __device__ __forceinline__ static void stage(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
-                                                 int tws, const C* pre, uint32_t twa) {
+                                                 int tws, const C* pre) {
         constexpr int REM = N / NS;
         constexpr int R = REM >= RMAX ? RMAX : REM;
         constexpr bool LAST = (NS * R == N);
@@ -311,24 +266,6 @@ struct LineFFT {
             if constexpr (SHARED_TW) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) a[r] = cmul(a[r], mul_root16<INV>(pw[r], (i * r * (16 / E)) & 15));
-            } else if constexpr (tw_in_tmem<NS>()) {
-                if constexpr (sizeof(T) == 4) {
-                    // two loads of 8 factors each, to keep fewer registers live
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        float tr[16];
-                        tmem_ld16(twa + 32 * tw_slot<NS>() + 16 * h, tr);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int r = 1 + 8 * h + i;
-                            if (r < R) {
-                                const C w = mkc(tr[2 * i], tr[2 * i + 1]);
-                                a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
-                            }
-                        }
-                    }
-                }
             } else if constexpr (NS > 1 && PRE) {
                 a[1] = INV ? cmulc(a[1], pre[ilog2c(NS)]) : cmul(a[1], pre[ilog2c(NS)]);
             } else if constexpr (NS > 1) {
@@ -348,7 +285,7 @@ struct LineFFT {
             line_sync<SYNC>();
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m) * SMS];
-            stage<NS * R>(v, sm, t, tw, tws, pre, twa);
+            stage<NS * R>(v, sm, t, tw, tws, pre);
         }
     }
 
@@ -358,14 +295,14 @@ struct LineFFT {
     // `tw` holds W_L^k of a length L = N * tws (tws = 1 unless the line is a
     // decimated part of a longer one).
     __device__ __forceinline__ static void run(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
-                                               int tws = 1, uint32_t twa = 0) {
+                                               int tws = 1) {
         C pre[PRE ? LOGN : 1];
         if constexpr (PRE) {
             // stage NS = 2^s (s >= 1): W_{2 NS}^(t mod NS) = W_L^((N / (2 NS)) (t mod NS) tws)
 #pragma unroll
             for (int s = 1; s < LOGN; ++s) pre[s] = tw[(int64_t)(N >> (s + 1)) * (t & ((1 << s) - 1)) * tws];
         }
-        stage<1>(v, sm, t, tw, tws, pre, twa);
+        stage<1>(v, sm, t, tw, tws, pre);
     }
 };
 

@@ -69,60 +69,4 @@ __device__ __forceinline__ void finalize_update(const double* tot, const SchemeP
     ctrl->iter = k + 1;
 }
 
-// The finalize step fused into a pass: every block has written its partial sums
-// partials[blockIdx][0..NV); each then counts itself in ctrl->arrivals, and the
-// block that arrives last (all partials are then visible) sums them over the
-// blocks in a fixed order (blocks strided over the threads, a shuffle tree, the
-// warps in order), runs the scalar recurrence and resets the count for the next
-// launch.  Call from every thread of every block, after the partials are written.
-template <int NV, int NT>
-__device__ __forceinline__ void finalize_last_block(const double* partials, const SchemeParams& P, Ctrl* ctrl,
-                                                    double* hist, int final_mode) {
-    __shared__ double tot[NV];
-    __shared__ double red[NT / 32 > 0 ? NT / 32 : 1][NV];
-    __shared__ int last;
-    __threadfence();   // publish this block's partials
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&ctrl->arrivals, 1u) + 1 == gridDim.x;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();   // acquire: the other blocks' partials, read through L2
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double x[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) x[v] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += NT)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) x[v] += __ldcg(partials + (int64_t)b * NV + v);
-    if constexpr (NT >= 32) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            for (int o = 16; o > 0; o >>= 1) x[v] += __shfl_down_sync(0xffffffffu, x[v], o);
-            if (lane == 0) red[warp][v] = x[v];
-        }
-        __syncthreads();
-        if (threadIdx.x < NV) {
-            double s = 0.0;
-            for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
-            tot[threadIdx.x] = s;
-        }
-    } else {   // a block narrower than a warp: thread 0 adds the threads' sums in order
-#pragma unroll
-        for (int v = 0; v < NV; ++v) red[0][v] = 0.0;
-        __syncthreads();
-        for (int i = 0; i < NT; ++i) {
-            if (threadIdx.x == i)
-#pragma unroll
-                for (int v = 0; v < NV; ++v) red[0][v] += x[v];
-            __syncthreads();
-        }
-        if (threadIdx.x < NV) tot[threadIdx.x] = red[0][threadIdx.x];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        finalize_update(tot, P, ctrl, hist, final_mode);
-        ctrl->arrivals = 0;
-    }
-}
-
 }  // namespace lsfft

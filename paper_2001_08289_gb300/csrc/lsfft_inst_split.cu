@@ -77,9 +77,7 @@ cudaError_t split_col_op(int op, const PassArgs<float>* A, cudaStream_t s, Geom*
             cudaError_t e = cudaFuncSetAttribute(col_pass_split<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  Cfg::SMEM);
             if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass_split<M>, Cfg::THREADS, Cfg::SMEM);
-            if (e == cudaSuccess && bps * Cfg::TMEM_COLS > 512) bps = 512 / Cfg::TMEM_COLS;
-            return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass_split<M>, Cfg::THREADS, Cfg::SMEM);
         }
         col_pass_split<M><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
         return cudaGetLastError();

@@ -31,7 +31,6 @@
 #include <cuda.h>   // CUtensorMap (the encoding itself goes through the runtime's driver entry point)
 
 #include "lsfft_fft.cuh"
-#include "lsfft_finalize.cuh"
 #include "lsfft_params.h"
 #include "lsfft_tma.cuh"
 
@@ -219,6 +218,7 @@ struct KConst {
     cx<T> iq_in, iq_out;        // initial Q = iq e per phase (two-phase media)
     T e[3];
     int scheme, green;
+    int real_coef;              // the Gamma-step coefficients g_a, g_b, g_a0, g_ce are real
 };
 
 // Compile-time integer (a scheme, a count) for code specialised outside a loop.
@@ -449,10 +449,6 @@ struct PassArgs {
     int grid_blocks;          // persistent grid size chosen by the host
     int packed;               // packed real layout (2-D row pass only; the strided pass sees two planes)
     KConst<T> k;
-    SchemeParams prm;         // FP64 constants of the scalar recurrence (fused finalize)
-    double* hist;             // history of the solve (fused finalize)
-    int fuse_fin;             // row pass: the last block runs the finalize step (2: sums and history
-                              // only, without the stop rule: pass timing of lsfft_launch_passes)
     long long wait_limit;     // bound of every mbarrier wait, in clock cycles
     int extra_tx;             // test hook: bytes announced but never delivered (0 in normal runs)
     CUtensorMap tmap;         // strided passes: TMA view of the planes (encoded by the host)
@@ -470,12 +466,7 @@ row_pass(const PassArgs<T> A) {
     constexpr int PS = Cfg::P::S, PX = Cfg::P::X;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int mode = A.mode;
-    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) {
-        // the solve has stopped: with the finalize fused here, this pass also tells the
-        // strided passes of the launch to skip
-        if (A.fuse_fin && blockIdx.x == 0 && threadIdx.x == 0) A.ctrl->skipB = 1;
-        return;
-    }
+    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;
 
     C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][LPB][PS]
     const int g = threadIdx.x / TL, t = threadIdx.x % TL;
@@ -793,9 +784,6 @@ row_pass(const PassArgs<T> A) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) dacc[i] = (double)acc[i] - (double)cmp[i];
     block_reduce_store<NV, Cfg::THREADS>(dacc, A.partials + (int64_t)blockIdx.x * NV);
-    if (A.fuse_fin)
-        finalize_last_block<NV, Cfg::THREADS>(A.partials, A.prm, A.ctrl, A.hist,
-                                              mode == MODE_ROW_OUTPUT || A.fuse_fin == 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -804,10 +792,69 @@ row_pass(const PassArgs<T> A) {
 // TRIG: Gamma(k) = k k^T/|k|^2 (Eq. J11), 0 if a component is at the Nyquist
 // index; FD: Gamma(k) = u u^H/|u|^2 with u_a = exp(2 pi i k_a/n_a) - 1.
 // ---------------------------------------------------------------------------
+// Real coefficients a, b, a0, ce (real sigma_1 and reference medium: every
+// packed-layout solve): the same step with real arithmetic on the coefficients,
+// and for the trigonometric symbol a real u = k, about half the instructions.
+template <typename T, int D>
+__device__ __forceinline__ void gamma_apply_real(cx<T> (&v)[D], const int (&ki)[3], const KConst<T>& K,
+                                                 const int* nn, const cx<T>* const* fd) {
+    using C = cx<T>;
+    bool zero = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) zero = zero && (ki[a] == 0);
+    if (zero) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) v[c] = mkc(K.g_a0.x * v[c].x + K.g_ce.x * K.e[c], K.g_a0.x * v[c].y);
+        return;
+    }
+    if (K.green == GREEN_TRIG) {
+        T k[D];
+        bool nyq = false;
+        T nrm = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int n = nn[a];
+            k[a] = (T)(ki[a] < n / 2 ? ki[a] : ki[a] - n);
+            nyq = nyq || (ki[a] == n / 2);
+            nrm += k[a] * k[a];
+        }
+        if (nyq) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) v[c] = cscale(v[c], K.g_a.x);
+            return;
+        }
+        C dot = mkc((T)0, (T)0);   // k . v
+#pragma unroll
+        for (int a = 0; a < D; ++a) dot = mkc(dot.x + k[a] * v[a].x, dot.y + k[a] * v[a].y);
+        const T sb = K.g_b.x / nrm;
+        const C proj = cscale(dot, sb);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            v[c] = mkc(K.g_a.x * v[c].x + proj.x * k[c], K.g_a.x * v[c].y + proj.y * k[c]);
+        return;
+    }
+    C u[D];
+    T nrm = 0;
+    C dot = mkc((T)0, (T)0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        u[a] = fd[a][ki[a]];
+        nrm += u[a].x * u[a].x + u[a].y * u[a].y;
+        dot = cadd(dot, cmulc(v[a], u[a]));    // conj(u_a) v_a
+    }
+    const C proj = cscale(dot, K.g_b.x / nrm);
+#pragma unroll
+    for (int c = 0; c < D; ++c) v[c] = cadd(cscale(v[c], K.g_a.x), cmul(proj, u[c]));
+}
+
 template <typename T, int D>
 __device__ __forceinline__ void gamma_apply_k(cx<T> (&v)[D], const int (&ki)[3], const KConst<T>& K, const int* nn,
                                               const cx<T>* const* fd) {
     using C = cx<T>;
+    if (K.real_coef) {
+        gamma_apply_real<T, D>(v, ki, K, nn, fd);
+        return;
+    }
     bool zero = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) zero = zero && (ki[a] == 0);

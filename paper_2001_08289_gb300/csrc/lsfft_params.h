@@ -45,8 +45,7 @@ struct Ctrl {
     int run;         // consecutive relative changes below tol
     int status;      // ST_*
     int fault;       // a bounded device wait gave up (the results are not valid)
-    unsigned int arrivals;   // row-pass blocks done with this launch (the last one finalizes)
-    int pad2;
+    int pad1, pad2;
     double prev[2];  // sigma_{k-1}
     double prev_norm;   // <|E_{k-1}|^2>
     double norm0;    // <|E_0|^2>

@@ -50,7 +50,7 @@ struct SplitRowCfg {
     static constexpr int X_BYTES = XP * 8;
     static constexpr int SMEM = STAGE_BYTES + MASK_BYTES + X_BYTES + 16;
     static constexpr int WARPS = THREADS / 32;
-    static constexpr int COLS_PER_WARP = 128;                   // twiddles 64, two parked lines 2 x 32
+    static constexpr int COLS_PER_WARP = 64;                    // two parked lines, 32 columns each
     static constexpr int TMEM_COLS = ((WARPS + 3) / 4) * COLS_PER_WARP;
     static constexpr bool SUPPORTED = (N == 4096 || N == 8192) && SMEM <= 227 * 1024 && TMEM_COLS <= 512;
     static constexpr int MINB = min_blocks(SMEM, THREADS);
@@ -70,10 +70,7 @@ struct SplitColCfg {
     static constexpr int SLOT_BYTES = M * W * 8;                // one plane of an item, dense [j][w]
     static constexpr int SLOT_WARPS = COMPUTE / 32;
     static constexpr int SMEM = NB * BUF + 64;                  // + six mbarriers
-    static constexpr int COLS_PER_WARP = 64;                    // twiddles of two stages, 32 columns each
-    static constexpr int TMEM_COLS = ((COMPUTE / 32 + 3) / 4) * COLS_PER_WARP;
-    static constexpr bool SUPPORTED = (M == 2048 || M == 4096) && SMEM <= 227 * 1024 && M % 256 == 0 &&
-                                      TMEM_COLS <= 512;
+    static constexpr bool SUPPORTED = (M == 2048 || M == 4096) && SMEM <= 227 * 1024 && M % 256 == 0;
 };
 
 // Scheme update of the packed real layout on one row, positions t + TL m of the
@@ -140,14 +137,11 @@ row_pass_split(const PassArgs<float> A) {
     using Cfg = SplitRowCfg<N>;
     using C = float2;
     constexpr int E = Cfg::E, TL = Cfg::TL, HP = Cfg::HP;
-    using FwdFFT = LineFFT<float, N, E, 16, false, false, 0, 1, true>;
-    using InvFFT = LineFFT<float, N, E, 16, true, false, 0, 1, true>;
+    using FwdFFT = LineFFT<float, N, E, 16, false>;
+    using InvFFT = LineFFT<float, N, E, 16, true>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int mode = A.mode;
-    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) {   // uniform: before any allocation
-        if (A.fuse_fin && blockIdx.x == 0 && threadIdx.x == 0) A.ctrl->skipB = 1;
-        return;
-    }
+    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;   // uniform: before any allocation
 
     C* St = reinterpret_cast<C*>(smem_raw);                                         // [4][HP]
     const uint8_t* Mb = smem_raw + Cfg::STAGE_BYTES;                                // [2][N]
@@ -171,10 +165,7 @@ row_pass_split(const PassArgs<float> A) {
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
-    const uint32_t twa = tmem_warp_addr(tmem_base_s, warp, Cfg::COLS_PER_WARP);
-    const uint32_t park_in = twa + 64, park_out = twa + 96;
-    FwdFFT::init_twiddles(t, twa);
-    tmem_wait_st();
+    const uint32_t park_in = tmem_warp_addr(tmem_base_s, warp, Cfg::COLS_PER_WARP), park_out = park_in + 32;
 
     // bulk copies need 16-byte aligned ends: checked once, a bad base is reported
     // and nothing is copied (the waits then run out and the solve reports a fault)
@@ -281,24 +272,21 @@ row_pass_split(const PassArgs<float> A) {
         __syncthreads();   // every thread has read the stage buffer and the mask rows
         if (t == 0 && pair + A.grid_blocks < M) prefetch(pair + A.grid_blocks);
 
-        // rows j and j + M (parked): inverse x-DFT, scheme update, forward x-DFT; one
-        // call site per transform (the kernel's code stays small for the instruction cache)
-#pragma unroll 1
-        for (int r = 0; r < 2; ++r) {
-            if (r == 1) {
-                tmem_wait_st();
-                tmem_fetch16(park_in, v0);
-            }
-            if (stage_x) InvFFT::run(v0, Xb, t, nullptr, 1, twa);
-            update_row(v0, r == 0 ? inc0 : inc1, pair + r * M);
-            if (outm) continue;
-            FwdFFT::run(v0, Xb, t, nullptr, 1, twa);
-            if (r == 0) tmem_park16(park_out, v0);
+        if (stage_x) InvFFT::run(v0, Xb, t, nullptr);
+        update_row(v0, inc0, pair);
+        if (!outm) {
+            FwdFFT::run(v0, Xb, t, nullptr);
+            tmem_park16(park_out, v0);
         }
+        tmem_wait_st();
+        tmem_fetch16(park_in, v0);
+        if (stage_x) InvFFT::run(v0, Xb, t, nullptr);
+        update_row(v0, inc1, pair + M);
         if (outm) {
             __syncthreads();   // the exchange line is reused by the next pair's transforms
             continue;
         }
+        FwdFFT::run(v0, Xb, t, nullptr);
         // forward butterfly: a = Z_j + Z_{j+M} now, b = (Z_j - Z_{j+M}) parked until a is stored
         {
             C v1[E];
@@ -327,9 +315,7 @@ row_pass_split(const PassArgs<float> A) {
     for (int i = 0; i < Cfg::NV; ++i) dacc[i] = (double)acc[i] - (double)cmp[i];
     block_reduce_store<Cfg::NV, Cfg::THREADS>(dacc, A.partials + (int64_t)blockIdx.x * Cfg::NV);
     if (fault) atomicExch(&A.ctrl->fault, 1);
-    if (A.fuse_fin)
-        finalize_last_block<Cfg::NV, Cfg::THREADS>(A.partials, A.prm, A.ctrl, A.hist,
-                                                   mode == MODE_ROW_OUTPUT || A.fuse_fin == 2);
+
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
@@ -348,8 +334,8 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
     using C = float2;
     constexpr int W = Cfg::W, NB = Cfg::NB, E = Cfg::E, TL = Cfg::TL, COMPUTE = Cfg::COMPUTE;
     constexpr int BUFC = Cfg::BUF / 8;
-    using FwdFFT = LineFFT<float, M, E, 16, false, false, COMPUTE, W, true>;
-    using InvFFT = LineFFT<float, M, E, 16, true, false, COMPUTE, W, true>;
+    using FwdFFT = LineFFT<float, M, E, 16, false, false, COMPUTE, W>;
+    using InvFFT = LineFFT<float, M, E, 16, true, false, COMPUTE, W>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (A.ctrl->skipB) return;   // uniform over the grid
     // TMA tile destinations need a 128-byte aligned base: the kernel declares no
@@ -362,12 +348,10 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
 
     C* Y = reinterpret_cast<C*>(smem_raw);
     const bool producer = threadIdx.x >= COMPUTE;
-    const int warp = threadIdx.x >> 5;
     const int w = threadIdx.x % W;
     const int t = (threadIdx.x / W) % TL;
     // mbarriers: full[b] at bar0 + 8 b, done[b] at bar0 + 24 + 8 b
     const uint32_t bar0 = smem_u32(smem_raw + NB * Cfg::BUF);
-    uint32_t& tmem_base_s = *reinterpret_cast<uint32_t*>(smem_raw + NB * Cfg::BUF + 48);   // after the mbarriers
     const int64_t G = (A.n_inner + W - 1) / W;   // column groups per half
     const int64_t n_items = 2 * G;
     const int64_t cid = blockIdx.x, ncl = gridDim.x;
@@ -396,10 +380,7 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc_warp(&tmem_base_s, Cfg::TMEM_COLS);
-    tmem_fence_before_sync();
     __syncthreads();
-    tmem_fence_after_sync();
     bool fault = false;
     if (producer) {
         if (leader) {
@@ -420,24 +401,22 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
         }
         __syncwarp();
     } else {
-        const uint32_t twa = tmem_warp_addr(tmem_base_s, warp, Cfg::COLS_PER_WARP);
-        FwdFFT::init_twiddles(t, twa);
-        tmem_wait_st();
         for (int64_t it = 0; it < my_items; ++it) {
             const int64_t item = cid + it * ncl;
             const int h = (int)(item / G);
-            C* B2[2] = {Y + (int)((2 * it) % NB) * BUFC, Y + (int)((2 * it + 1) % NB) * BUFC};
+            C* const Bx = Y + (int)((2 * it) % NB) * BUFC;       // plane X of the item
+            C* const By = Y + (int)((2 * it + 1) % NB) * BUFC;   // plane Y
             // forward DFTs of both planes in place, results back in natural order
 #pragma unroll 1
             for (int p = 0; p < 2; ++p) {
                 const int64_t qq = 2 * it + p;
                 const int b = (int)(qq % NB);
-                C* Bp = B2[p];
+                C* Bp = Y + b * BUFC;
                 if (!mbar_wait(bar0 + 8 * b, (uint32_t)((qq / NB) & 1), A.wait_limit)) fault = true;
                 C v[E];
 #pragma unroll
                 for (int m = 0; m < E; ++m) v[m] = Bp[(t + TL * m) * W + w];
-                FwdFFT::run(v, Bp + w, t, nullptr, 1, twa);
+                FwdFFT::run(v, Bp + w, t, nullptr);
                 line_sync<COMPUTE>();   // every thread has read its last-stage inputs
 #pragma unroll
                 for (int m = 0; m < E; ++m) Bp[(t + TL * m) * W + w] = v[m];
@@ -447,11 +426,11 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
             const int kx0 = (int)((item % G) * W);
             for (int pidx = threadIdx.x; pidx < M * W; pidx += COMPUTE) {
                 const int kl = pidx / W, wc = pidx % W;
-                C q[2] = {B2[0][pidx], B2[1][pidx]};
+                C q[2] = {Bx[pidx], By[pidx]};
                 const int ki[3] = {kx0 + wc, 2 * kl + h, 0};
                 gamma_apply<float, 2>(q, ki, A);
-                B2[0][pidx] = q[0];
-                B2[1][pidx] = q[1];
+                Bx[pidx] = q[0];
+                By[pidx] = q[1];
             }
             line_sync<COMPUTE>();
             // inverse DFTs in place, plane Y then X; each slot is handed to the
@@ -460,11 +439,11 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
             for (int p = 1; p >= 0; --p) {
                 const int64_t qq = 2 * it + p;
                 const int b = (int)(qq % NB);
-                C* Bp = B2[p];
+                C* Bp = Y + b * BUFC;
                 C v[E];
 #pragma unroll
                 for (int m = 0; m < E; ++m) v[m] = Bp[(t + TL * m) * W + w];
-                InvFFT::run(v, Bp + w, t, nullptr, 1, twa);
+                InvFFT::run(v, Bp + w, t, nullptr);
                 line_sync<COMPUTE>();
 #pragma unroll
                 for (int m = 0; m < E; ++m) Bp[(t + TL * m) * W + w] = v[m];
@@ -476,10 +455,6 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
         }
     }
     if (fault) atomicExch(&A.ctrl->fault, 1);
-    tmem_fence_before_sync();
-    __syncthreads();
-    tmem_fence_after_sync();
-    if (warp == 0) tmem_dealloc_warp(tmem_base_s, Cfg::TMEM_COLS);
 }
 
 }  // namespace lsfft

@@ -9,7 +9,8 @@
 // [63:40] epoch, [39:32] pass kind, [31:0] next item ticket.  A block claims an
 // item with one atomicAdd on the word, which returns the epoch, pass and ticket
 // consistently; tickets beyond the pass's item count are dropped.  After an
-// item, every thread fences its writes and the block counts the item as done;
+// item, a block barrier and one GPU-scope fence publish the block's writes and
+// the block counts the item as done;
 // the block that completes the last item of an epoch makes the transition:
 //   row pass done     -> finalize (FP64 sums of the row items' partials in a
 //                        fixed order, sigma_k of Eq. J13, stop rule) -> strided pass
@@ -40,6 +41,7 @@ namespace {
 
 constexpr int SW_THREADS = 256;
 constexpr int SW_NV = 9;   // 4 d + 1 volume sums, d = 2
+constexpr int CLAIM = 4;   // consecutive items claimed at once when a pass has many
 
 enum { PH_FIRST = 0, PH_ROW = 1, PH_COL = 2, PH_OUT = 3 };
 
@@ -297,33 +299,67 @@ __host__ __device__ constexpr unsigned long long word_of(unsigned long long epoc
 __global__ void __launch_bounds__(SW_THREADS, 2)
 sweep_kernel(SweepJob* __restrict__ jobs, int njobs, SweepGlobal* __restrict__ glob, long long idle_limit_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_job, s_item, s_phase, s_last;
+    __shared__ int s_job, s_item, s_nitems, s_phase, s_last;
     unsigned start = blockIdx.x;
     unsigned long long t_idle = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_job = -1;
-            if (*(volatile int*)&glob->jobs_done >= njobs || *(volatile int*)&glob->error) {
-                s_job = -2;
-            } else {
-                for (int c = 0; c < njobs && s_job == -1; ++c) {
-                    const int j = (int)((start + c) % (unsigned)njobs);
+        // the first warp looks for work: its 32 lanes probe 32 solves per round trip,
+        // the claimable ones (by ballot) are tried in order with one atomicAdd each
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int found = -1, item = 0, phase = 0, nitems = 1;
+            bool stop = false;
+            if (*(volatile int*)&glob->jobs_done >= njobs || *(volatile int*)&glob->error) stop = true;
+            for (int c0 = 0; c0 < njobs && found < 0 && !stop; c0 += 32) {
+                const int j = (int)((start + (unsigned)(c0 + lane)) % (unsigned)njobs);
+                bool ok = false;
+                if (c0 + lane < njobs) {
                     SweepJob& J = jobs[j];
-                    if (*(volatile int*)&J.finished) continue;
                     const unsigned long long wd = *(volatile unsigned long long*)&J.word;
                     const int ph = (int)((wd >> 32) & 0xff);
-                    if ((wd & 0xffffffffull) >= (unsigned long long)pass_items(J, ph)) continue;
-                    const unsigned long long old = atomicAdd(&J.word, 1ull);
-                    const int ph2 = (int)((old >> 32) & 0xff);
-                    const unsigned long long ticket = old & 0xffffffffull;
-                    if (ticket < (unsigned long long)pass_items(J, ph2)) {
-                        s_job = j;
-                        s_item = (int)ticket;
-                        s_phase = ph2;
-                        start = (unsigned)j;   // stay with this solve while it has items
+                    ok = !*(volatile int*)&J.finished && (wd & 0xffffffffull) < (unsigned long long)pass_items(J, ph);
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, ok);
+                while (mask && found < 0) {
+                    const int src = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    int got = -1, it2 = 0, ph2 = 0, k2 = 0;
+                    if (lane == src) {
+                        SweepJob& J = jobs[j];
+                        // passes with many items hand out CLAIM consecutive items per atomic
+                        const int cnt = pass_items(J, (int)((*(volatile unsigned long long*)&J.word >> 32) & 0xff));
+                        const unsigned long long want = cnt >= 16 * CLAIM ? CLAIM : 1;
+                        const unsigned long long old = atomicAdd(&J.word, want);
+                        ph2 = (int)((old >> 32) & 0xff);
+                        const unsigned long long ticket = old & 0xffffffffull;
+                        const unsigned long long count = (unsigned long long)pass_items(J, ph2);
+                        if (ticket < count) {
+                            got = j;
+                            it2 = (int)ticket;
+                            k2 = (int)((ticket + want <= count ? want : count - ticket));
+                        }
+                    }
+                    got = __shfl_sync(0xffffffffu, got, src);
+                    it2 = __shfl_sync(0xffffffffu, it2, src);
+                    ph2 = __shfl_sync(0xffffffffu, ph2, src);
+                    k2 = __shfl_sync(0xffffffffu, k2, src);
+                    if (got >= 0) {
+                        found = got;
+                        item = it2;
+                        phase = ph2;
+                        nitems = k2;
                     }
                 }
-                if (s_job == -1) {
+            }
+            if (lane == 0) {
+                s_job = stop ? -2 : found;
+                s_item = item;
+                s_nitems = nitems;
+                s_phase = phase;
+                if (found >= 0) {
+                    start = (unsigned)found;   // stay with this solve while it has items
+                    t_idle = 0;
+                } else if (!stop) {
                     unsigned long long now;
                     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
                     if (t_idle == 0) t_idle = now;
@@ -331,11 +367,10 @@ sweep_kernel(SweepJob* __restrict__ jobs, int njobs, SweepGlobal* __restrict__ g
                         atomicExch(&glob->error, 1);
                         s_job = -2;
                     }
-                } else {
-                    t_idle = 0;
                 }
+                __threadfence();   // acquire: the claimed pass's input was published before its epoch
             }
-            __threadfence();   // acquire: the claimed pass's input was published before its epoch
+            start = __shfl_sync(0xffffffffu, start, 0);
         }
         __syncthreads();
         const int j = s_job;
@@ -346,14 +381,17 @@ sweep_kernel(SweepJob* __restrict__ jobs, int njobs, SweepGlobal* __restrict__ g
             continue;
         }
         SweepJob& J = jobs[j];
-        const int phase = s_phase;
-        if (phase == PH_COL) col_item(J, s_item, smem);
-        else row_item(J, s_item, phase, smem);
-        __threadfence();   // every thread publishes its writes before the item is counted
-        __syncthreads();
+        const int phase = s_phase, nit = s_nitems;
+        for (int i = 0; i < nit; ++i) {
+            if (i > 0) __syncthreads();   // shared memory of the previous item is free
+            if (phase == PH_COL) col_item(J, s_item + i, smem);
+            else row_item(J, s_item + i, phase, smem);
+        }
+        __syncthreads();   // the block's writes of the items are done ...
         if (threadIdx.x == 0) {
-            const unsigned prev = atomicAdd(&J.completed, 1u);
-            s_last = prev + 1 == (unsigned)pass_items(J, phase);
+            __threadfence();   // ... and published (cumulatively, through the barrier) before the count
+            const unsigned prev = atomicAdd(&J.completed, (unsigned)nit);
+            s_last = prev + (unsigned)nit == (unsigned)pass_items(J, phase);
         }
         __syncthreads();
         if (!s_last) continue;

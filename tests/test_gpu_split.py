@@ -32,6 +32,7 @@ def L():
 def _compare(L, mask, s1, scheme, iters, e=(1.0, 0.0), green="trig", ab=(0.25, 4.0), sigma=None):
     e = np.array(e)
     with L.Grid(mask) as g:
+        g.set_column_split(True)
         if sigma is not None:
             g.set_sigma_field(sigma)
         r = g.solve(s1, e, scheme=scheme, precision="fp32", green=green, tol=0.0, max_iter=iters,

@@ -32,7 +32,7 @@ def test_autotune_times_candidates_and_applies(L, n, candidates, tmp_path):
         assert t["candidates"] == candidates and t["check_every"] in (4, 8, 16, 32, 64)
         assert t["column_split"] in (0, 1) and t["ms_per_iter"] > 0
         if n < 4096:
-            assert t["column_split"] == 1   # only one layout exists
+            assert t["column_split"] == 0   # one layout exists: the default stays
         path = str(tmp_path / "tune.json")
         kw_t = tune.tuned(g, 10.0, [1.0, 0.0], path=path, **kw)
         r1 = g.solve(10.0, [1.0, 0.0], **kw_t)
