@@ -33,8 +33,7 @@ cudaError_t row_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
             if (e != cudaSuccess) return e;
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, row_pass<T, N, D>, Cfg::THREADS, Cfg::SMEM);
         }
-        row_pass<T, N, D><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
-        return cudaGetLastError();
+        return launch_pdl(row_pass<T, N, D>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s, *A);
     }
 }
 
@@ -64,8 +63,8 @@ cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
             cfg.dynamicSmemBytes = Cfg::SMEM;
             return cudaOccupancyMaxActiveClusters(&max_clusters, (const void*)col_pass_cluster<T, N>, &cfg);
         }
-        col_pass_cluster<T, N><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
-        return cudaGetLastError();
+        return launch_pdl(col_pass_cluster<T, N>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
+                          *A);
     } else {
         using Cfg = ColCfg<T, N, D>;
         static int bps = 0;
@@ -89,8 +88,8 @@ cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
                 return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass<T, N, D>, Cfg::THREADS,
                                                                      Cfg::SMEM);
             }
-            col_pass<T, N, D><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
-            return cudaGetLastError();
+            return launch_pdl(col_pass<T, N, D>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
+                              *A);
         }
     }
 }

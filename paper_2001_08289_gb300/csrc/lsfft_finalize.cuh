@@ -23,16 +23,19 @@ __device__ __forceinline__ void finalize_update(const double* tot, const SchemeP
         je_re += tot[4 * c + 2] * P.e[c];
         je_im += tot[4 * c + 3] * P.e[c];
     }
-    const double den = ee_re * ee_re + ee_im * ee_im;
-    const double s_re = (je_re * ee_re + je_im * ee_im) / den;
-    const double s_im = (je_im * ee_re - je_re * ee_im) / den;
+    // (one reciprocal and one square root: FP64 division and sqrt are long
+    // instruction sequences on this GPU's narrow FP64 pipe, and this thread is
+    // on every iteration's critical path)
+    const double inv_den = 1.0 / (ee_re * ee_re + ee_im * ee_im);
+    const double s_re = (je_re * ee_re + je_im * ee_im) * inv_den;
+    const double s_im = (je_im * ee_re - je_re * ee_im) * inv_den;
     const double norm = tot[4 * d] * P.inv_ntot;
     const int k = ctrl->iter;
-    const double mag = sqrt(s_re * s_re + s_im * s_im);
+    const double mag2 = s_re * s_re + s_im * s_im;
     double rel = INFINITY;
-    if (k >= 1 && mag != 0.0) {
+    if (k >= 1 && mag2 != 0.0) {
         const double dr = s_re - ctrl->prev[0], di = s_im - ctrl->prev[1];
-        rel = sqrt(dr * dr + di * di) / mag;
+        rel = sqrt((dr * dr + di * di) / mag2);
     }
     hist[(int64_t)k * HIST_STRIDE + 0] = s_re;
     hist[(int64_t)k * HIST_STRIDE + 1] = s_im;

@@ -32,8 +32,8 @@ cudaError_t split_row_sch(int op, const PassArgs<float>* A, cudaStream_t s, Geom
             if (e == cudaSuccess && bps * Cfg::TMEM_COLS > 512) bps = 512 / Cfg::TMEM_COLS;
             return e;
         }
-        row_pass_split<N, SCH><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
-        return cudaGetLastError();
+        return launch_pdl(row_pass_split<N, SCH>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
+                          *A);
     }
 }
 
@@ -79,8 +79,7 @@ cudaError_t split_col_op(int op, const PassArgs<float>* A, cudaStream_t s, Geom*
             if (e != cudaSuccess) return e;
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass_split<M>, Cfg::THREADS, Cfg::SMEM);
         }
-        col_pass_split<M><<<(unsigned)A->grid_blocks, Cfg::THREADS, Cfg::SMEM, s>>>(*A);
-        return cudaGetLastError();
+        return launch_pdl(col_pass_split<M>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s, *A);
     }
 }
 

@@ -32,6 +32,8 @@
 
 #include "lsfft_fft.cuh"
 #include "lsfft_params.h"
+#include "lsfft_pdl.cuh"
+#include "lsfft_reduce.cuh"
 #include "lsfft_tma.cuh"
 
 namespace lsfft {
@@ -179,28 +181,22 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], double* __
         return;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        double x = acc[v];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if constexpr (NT == 32) {   // one warp: its sum is the block's
-            if (lane == 0) out[v] = x;
-        } else {
-            if (lane == 0) red[warp][v] = x;
-        }
+    constexpr int LOW = 32 / pow2_at_least(NV) - 1;   // lanes with these bits zero hold distinct sums
+    int idx;
+    const double x = warp_sum_scatter<NV>(acc, idx);
+    if ((lane & LOW) == 0 && idx < NV) {
+        if constexpr (NT == 32) out[idx] = x;   // one warp: its sum is the block's
+        else red[warp][idx] = x;
     }
     if constexpr (NT == 32) return;
     __syncthreads();
     if (warp == 0) {
         const int nw = (blockDim.x + 31) >> 5;
+        double y[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double x = lane < nw ? red[lane][v] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) out[v] = x;
-        }
+        for (int v = 0; v < NV; ++v) y[v] = lane < nw ? red[lane][v] : 0.0;
+        const double s = warp_sum_scatter<NV>(y, idx);
+        if ((lane & LOW) == 0 && idx < NV) out[idx] = s;
     }
 }
 
@@ -465,6 +461,8 @@ row_pass(const PassArgs<T> A) {
     constexpr int E = Cfg::E, TL = Cfg::TL, LPB = Cfg::LPB, NV = 4 * D + 1;
     constexpr int PS = Cfg::P::S, PX = Cfg::P::X;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
+    pdl_trigger();
     const int mode = A.mode;
     if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;
 
@@ -920,6 +918,8 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
     using C = cx<T>;
     constexpr int E = Cfg::E, TL = Cfg::TL, COLS = Cfg::COLS, XP = Cfg::XP, EPC = Cfg::EPC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    pdl_wait();
+    pdl_trigger();
     if (A.ctrl->skipB) return;
     const int mode = A.mode;
 

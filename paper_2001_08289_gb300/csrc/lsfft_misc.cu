@@ -5,6 +5,8 @@
 
 #include "lsfft_finalize.cuh"
 #include "lsfft_misc.h"
+#include "lsfft_pdl.cuh"
+#include "lsfft_reduce.cuh"
 
 namespace lsfft {
 
@@ -40,51 +42,57 @@ __global__ void init_state_kernel(cx<T>* __restrict__ X, cx<T>* __restrict__ S, 
     }
 }
 
-// One block of FIN_THREADS threads after each row pass.  Sums partials[b][v]
-// over the row pass's blocks in a fixed order (deterministic), then thread 0
-// runs the scalar recurrence.  (Running this in the last block of the row pass
-// itself, found by an atomic arrival count, measured slower: the row kernel
-// lost 30 us at 8192^2 from the extra code alone.)
-constexpr int FIN_THREADS = 256;
+// One block after each row pass, of up to FIN_WARPS warps (one warp when the
+// row pass ran at most 64 blocks): sums partials[b][v] over the row pass's
+// blocks in a fixed order (lane-strided running sums, warp reduce-scatter,
+// then across the warps), then thread 0 runs the scalar recurrence.  The FP64
+// additions on the critical path are what this kernel costs on small grids.
+// (Running it in the last block of the row pass itself, found by an atomic
+// arrival count, measured slower: the row kernel lost 30 us at 8192^2 from the
+// extra code alone.)
+constexpr int FIN_WARPS = 8;
 
-__global__ void __launch_bounds__(FIN_THREADS)
+__global__ void __launch_bounds__(FIN_WARPS * 32)
 finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const SchemeParams P,
                 Ctrl* __restrict__ ctrl, double* __restrict__ hist, int final_mode) {
     constexpr int NVMAX = 16;   // nv = 4 d + 1 <= 13
     __shared__ double tot[NVMAX];
-    __shared__ double red[FIN_THREADS / 32][NVMAX];
+    __shared__ double red[FIN_WARPS][NVMAX];
+    pdl_wait();
+    pdl_trigger();
     if (!final_mode && ctrl->done) {
         if (threadIdx.x == 0) ctrl->skipB = 1;
         return;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // every value at once (its loads in flight together), each in the same
-    // fixed order: blocks strided over the threads, a shuffle tree, the warps
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double x[NVMAX];
 #pragma unroll
     for (int v = 0; v < NVMAX; ++v) x[v] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += FIN_THREADS) {
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         const double* pb = partials + (int64_t)b * nv;
 #pragma unroll
         for (int v = 0; v < NVMAX; ++v)
             if (v < nv) x[v] += pb[v];
     }
+    int idx;
+    const double s = warp_sum_scatter<NVMAX>(x, idx);   // lane pairs share an index
+    if ((lane & 1) == 0) red[warp][idx] = s;
+    __syncthreads();
+    if (warp == 0) {
+        double y[NVMAX];
 #pragma unroll
-    for (int v = 0; v < NVMAX; ++v) {
-        if (v < nv) {
-            for (int o = 16; o > 0; o >>= 1) x[v] += __shfl_down_sync(0xffffffffu, x[v], o);
-            if (lane == 0) red[warp][v] = x[v];
-        }
+        for (int v = 0; v < NVMAX; ++v) y[v] = lane < nw ? red[lane][v] : 0.0;
+        const double t = warp_sum_scatter<NVMAX>(y, idx);
+        if ((lane & 1) == 0) tot[idx] = t;
+        __syncwarp();
+        if (lane == 0) finalize_update(tot, P, ctrl, hist, final_mode);
     }
-    __syncthreads();
-    if (threadIdx.x < nv) {
-        double s = 0.0;
-        for (int w = 0; w < FIN_THREADS / 32; ++w) s += red[w][threadIdx.x];
-        tot[threadIdx.x] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    finalize_update(tot, P, ctrl, hist, final_mode);
+}
+
+static int finalize_threads(int nblocks) {
+    // one warp per 64 row-pass blocks, at most FIN_WARPS
+    const int w = (nblocks + 63) / 64;
+    return 32 * (w < 1 ? 1 : w > FIN_WARPS ? FIN_WARPS : w);
 }
 
 template <typename T>
@@ -99,8 +107,8 @@ cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, cons
 
 cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
                             double* hist, int final_mode, cudaStream_t s) {
-    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(partials, nblocks, nv, prm, ctrl, hist, final_mode);
-    return cudaGetLastError();
+    return launch_pdl(finalize_kernel, dim3(1), dim3(finalize_threads(nblocks)), 0, s, partials, nblocks, nv, prm,
+                      ctrl, hist, final_mode);
 }
 
 // Small device-to-host transfers (the control block, the history) written by

@@ -1,0 +1,40 @@
+// Programmatic dependent launch for the kernels of one iteration.
+//
+// A kernel launched by launch_pdl() may be scheduled while the kernel before
+// it in the stream is still running (its blocks are placed as soon as every
+// block of the previous kernel has executed pdl_trigger() or exited), which
+// hides the launch latency between the short passes of small grids.  Every
+// such kernel calls pdl_wait() before its first memory access: it returns once
+// the previous kernel has completed and its writes are visible, so the passes
+// still see each other's results in stream order, and since every kernel in the
+// chain waits before it can complete, the ordering is transitive.  A kernel
+// launched without the attribute (or with nothing before it) passes pdl_wait()
+// at once.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+
+namespace lsfft {
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+}  // namespace lsfft

@@ -140,6 +140,8 @@ row_pass_split(const PassArgs<float> A) {
     using FwdFFT = LineFFT<float, N, E, 16, false>;
     using InvFFT = LineFFT<float, N, E, 16, true>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();   // before any access and before the tensor-memory allocation
+    pdl_trigger();
     const int mode = A.mode;
     if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;   // uniform: before any allocation
 
@@ -337,6 +339,8 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
     using FwdFFT = LineFFT<float, M, E, 16, false, false, COMPUTE, W>;
     using InvFFT = LineFFT<float, M, E, 16, true, false, COMPUTE, W>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    pdl_wait();
+    pdl_trigger();
     if (A.ctrl->skipB) return;   // uniform over the grid
     // TMA tile destinations need a 128-byte aligned base: the kernel declares no
     // static shared variable, so the dynamic region starts at the window's origin.
