@@ -125,6 +125,10 @@ struct lsfft_grid {
     int64_t N = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;        // created by the library when the caller passed NULL
+    // the finalize step of each update runs on a stream of its own, beside the
+    // strided pass (which does not read its result), joined before the next row pass
+    cudaStream_t fin_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     int sm_count = 0;
     uint8_t* mask = nullptr;
@@ -176,6 +180,13 @@ struct lsfft_grid {
 };
 
 namespace {
+
+// Both of the grid's streams (the finalize stream is joined into the main one
+// after every update, but not on an error path).
+void sync_grid(lsfft_grid* g) {
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    if (g->fin_stream) cudaStreamSynchronize(g->fin_stream);
+}
 
 void clear_graphs(lsfft_grid* g) {
     for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
@@ -376,6 +387,9 @@ int create_common(int d, const int64_t n[3], const uint8_t* mask, bool on_device
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&g->ev1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_check, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->fin_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) rc = fail_cuda(e, "create_grid");
     if (rc == LSFFT_OK) rc = build_tables(g);
     if (rc == LSFFT_OK) {
@@ -765,15 +779,27 @@ cudaError_t launch_cols(lsfft_grid* g, int st) {
     return col_launch<T>(g, 1, &Y);
 }
 
-// One update: the row pass, the finalize step (sums, sigma_k, stop rule) and
-// the strided pass(es).
+// One update: the row pass, then the finalize step (sums, sigma_k, stop rule)
+// and the strided pass(es) side by side, joined before the next update.  The
+// strided passes need only `skipB`, which the row pass sets when it finds the
+// solve already done (the finalize step of this update may set `done`, after
+// which this update still completes, as the stop rule intends); the finalize
+// step reads the row pass's partial sums, which the next row pass overwrites,
+// hence the join.  On small grids this takes the finalize (a few microseconds
+// of dependent loads and FP64 scalar work) off the critical path.
 template <typename T>
 cudaError_t launch_iteration(lsfft_grid* g, int st, int nblocks, int row_mode) {
     cudaError_t e = launch_row<T>(g, st, row_mode, nullptr);
     if (e != cudaSuccess) return e;
-    e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 0, g->stream);
+    e = cudaEventRecord(g->ev_fork, g->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->fin_stream, g->ev_fork, 0);
+    if (e == cudaSuccess)
+        e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 0, g->fin_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_join, g->fin_stream);
     if (e != cudaSuccess) return e;
-    return launch_cols<T>(g, st);
+    e = launch_cols<T>(g, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(g->stream, g->ev_join, 0);
 }
 
 // The iteration graph bakes the scheme constants into its kernel parameters, so
@@ -862,7 +888,7 @@ int start_solve(lsfft_grid* g, int st) {
 
 // Drop a solve that failed: wait for its work and release its output buffer.
 void abandon_solve(lsfft_grid* g) {
-    cudaStreamSynchronize(g->stream);
+    sync_grid(g);
     cudaGetLastError();
     big_free(g->cur_E);
     g->cur_E = nullptr;
@@ -1037,7 +1063,7 @@ int lsfft_create_grid_device(int d, const int64_t n[3], const uint8_t* phase_mas
 
 void lsfft_destroy_grid(lsfft_grid* g) {
     if (!g) return;
-    if (g->stream) cudaStreamSynchronize(g->stream);
+    sync_grid(g);
     clear_graphs(g);
     cudaFree(g->mask);
     big_free(g->X);
@@ -1056,6 +1082,9 @@ void lsfft_destroy_grid(lsfft_grid* g) {
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     if (g->ev_check) cudaEventDestroy(g->ev_check);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
+    if (g->fin_stream) cudaStreamDestroy(g->fin_stream);
     if (g->hist_host) cudaFreeHost(g->hist_host);
     big_free(g->cur_E);
     cudaFree(g->sigma64);
@@ -1464,7 +1493,7 @@ int lsfft_set_column_split(lsfft_grid* g, int split) {
         g_last_error = "lsfft_set_column_split: null grid";
         return LSFFT_EINVAL;
     }
-    if (g->stream) cudaStreamSynchronize(g->stream);
+    sync_grid(g);
     clear_graphs(g);
     g->no_split = split == 0;
     g->bench_prec = -1;
@@ -1522,7 +1551,7 @@ int lsfft_debug_inject(lsfft_grid* g, int kind) {
         g_last_error = "lsfft_debug_inject: null grid or unknown kind";
         return LSFFT_EINVAL;
     }
-    if (g->stream) cudaStreamSynchronize(g->stream);
+    sync_grid(g);
     clear_graphs(g);
     g->inject_tx = kind == 1 ? 16 : 0;
     g->wait_limit = kind == 1 ? 20000000LL : MBAR_WAIT_LIMIT;
@@ -1534,7 +1563,7 @@ int lsfft_set_sigma_field(lsfft_grid* g, const lsfft_c128* sigma, int on_device,
         g_last_error = "null grid";
         return LSFFT_EINVAL;
     }
-    if (g->stream) cudaStreamSynchronize(g->stream);
+    sync_grid(g);
     clear_graphs(g);
     cudaFree(g->sigma64);
     cudaFree(g->sigma_t);

@@ -464,7 +464,12 @@ row_pass(const PassArgs<T> A) {
     pdl_wait();
     pdl_trigger();
     const int mode = A.mode;
-    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;
+    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) {   // uniform: before any allocation or barrier
+        // the solve stopped before this update: its strided passes skip as well
+        // (they run beside the finalize step and read only this flag)
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.ctrl->skipB = 1;
+        return;
+    }
 
     C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][LPB][PS]
     const int g = threadIdx.x / TL, t = threadIdx.x % TL;

@@ -40,7 +40,7 @@ struct SchemeParams {
 
 struct Ctrl {
     int done;        // stop criterion met: later row passes and finalizes skip
-    int skipB;       // set by a finalize that found `done`: later strided passes skip
+    int skipB;       // set by a row pass (or finalize) that found `done`: later strided passes skip
     int iter;        // number of sigma_k evaluated so far
     int run;         // consecutive relative changes below tol
     int status;      // ST_*

@@ -143,7 +143,12 @@ row_pass_split(const PassArgs<float> A) {
     pdl_wait();   // before any access and before the tensor-memory allocation
     pdl_trigger();
     const int mode = A.mode;
-    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) return;   // uniform: before any allocation
+    if (mode != MODE_ROW_OUTPUT && A.ctrl->done) {   // uniform: before any allocation or barrier
+        // the solve stopped before this update: its strided passes skip as well
+        // (they run beside the finalize step and read only this flag)
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.ctrl->skipB = 1;
+        return;
+    }
 
     C* St = reinterpret_cast<C*>(smem_raw);                                         // [4][HP]
     const uint8_t* Mb = smem_raw + Cfg::STAGE_BYTES;                                // [2][N]
