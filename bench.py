@@ -393,6 +393,20 @@ def run_ours(args, sigmas):
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
             "per_launch_alg_bytes": passes[dom]["alg_bytes"], "per_launch_ms": passes[dom]["ms"]}
 
+    # the arithmetic ceiling beside the HBM one: the passes' FFT flops (5 n log2 n per
+    # complex line transform, forward and inverse) against the FP32 FMA rate measured
+    # on this GPU now (plain and paired fma.rn.f32x2 forms)
+    fma_plain = L.lsfft_fma_peak(False, 3)
+    fma_paired = L.lsfft_fma_peak(True, 3)
+    fma_peak = max(fma_plain, fma_paired)
+    lines = {"row_pass": n if layout["packed"] else 2 * n, "col_pass": (n + 2) if layout["packed"] else 2 * n}
+    alu = {"fp32_fma_tflops_measured": round(fma_plain, 2), "fp32_fma_paired_tflops_measured": round(fma_paired, 2),
+           "flops_convention": "5 n log2 n per complex line transform, two transforms per line per pass"}
+    for kn in ("row_pass", "col_pass"):
+        fl = 2 * lines[kn] * 5.0 * n * math.log2(n)
+        tf = fl / (passes[f"{kn}|ms"]["ms"] * 1e-3) / 1e12
+        alu[kn] = {"fft_flops_per_launch": int(fl), "achieved_tflops": round(tf, 2), "frac": round(tf / fma_peak, 4)}
+
     # comparison only: the same MS update written with torch.fft (cuFFT), per update
     cufft = cufft_ms_update(n, green=args.green)
     ours_ms = passes["row_pass|ms"]["ms"] + passes["col_pass|ms"]["ms"]
@@ -464,7 +478,8 @@ def run_ours(args, sigmas):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if layout["packed"] else "c64",
             "data": "synthetic", "layout": "packed real (E_x + i E_y in one complex plane)" if layout["packed"]
             else "complex component planes",
-            "config": workload_config(args, sigmas), "roofline": roof, "gpu_launches": int(launches),
+            "config": workload_config(args, sigmas), "roofline": roof, "alu_ceiling": alu,
+            "gpu_launches": int(launches),
             "clocks": clk, "e2e": e2e,
             "time_to_tol": {"per_sigma1": per, "time_ratio": speed,
                             "true_error_reference": {str(k): {"sigma_star": [v[0].real, v[0].imag], "spread": v[1]}

@@ -311,6 +311,15 @@ int lsfft_prepare(lsfft_grid *grid, lsfft_c128 sigma1, const double *e, const ls
  * count < 0, or a grid without a prepared state (or whose last solve stopped). */
 int lsfft_launch_passes(lsfft_grid *grid, int kind, int count);
 
+/* Benchmarking: the FP32 FMA throughput of the current device, the ceiling
+ * against which the arithmetic of the FFT passes is reported.  Runs a kernel
+ * of 8 independent FMA chains per thread (`paired` = 1: the paired
+ * fma.rn.f32x2 form, two FMAs per instruction) on every SM, `reps` timed
+ * launches after one warm-up, and writes the best rate in TFLOP/s (2 flops
+ * per FMA) to *tflops.  Synchronises the device's legacy stream.  EINVAL for a
+ * null pointer or reps < 1; ECUDA on a CUDA error. */
+int lsfft_fma_peak(int paired, int reps, double *tflops);
+
 /* Estimate of the pole interval [-beta, -alpha] (section "Estimating the
  * parameters alpha and beta").  The singularities of sigma_*(sigma_1) are the
  * poles 1 - 1/m_n with m_n the eigenvalues of chi Gamma_1 chi weighted by

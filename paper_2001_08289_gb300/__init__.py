@@ -27,7 +27,7 @@ __all__ = [
     "lsfft_version", "lsfft_last_error", "lsfft_strerror", "lsfft_create_grid", "lsfft_create_grid_device",
     "lsfft_destroy_grid", "lsfft_default_opts", "lsfft_solve", "lsfft_copy_field", "lsfft_copy_field_async",
     "lsfft_free_result",
-    "lsfft_prepare", "lsfft_launch_passes", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
+    "lsfft_prepare", "lsfft_launch_passes", "lsfft_fma_peak", "lsfft_field_averages_noalloc", "lsfft_lanczos_hull",
     "lsfft_tridiag_gauss", "lsfft_set_sigma_field", "lsfft_gradient", "lsfft_solve_batch", "solve_batch",
     "lsfft_solve_sweep", "solve_sweep",
     "lsfft_substitution_rates", "lsfft_debug_inject", "lsfft_effective_tensor", "lsfft_set_column_split",
@@ -119,6 +119,7 @@ def load_library():
     lib.lsfft_free_result.restype = None
     lib.lsfft_prepare.argtypes = [C.c_void_p, _C128, C.POINTER(C.c_double), C.POINTER(Opts)]
     lib.lsfft_launch_passes.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    lib.lsfft_fma_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.lsfft_field_averages_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64), C.c_void_p, C.c_int, C.c_void_p,
                                                  _C128, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]
     lib.lsfft_noalloc_last_error.restype = C.c_char_p
@@ -386,6 +387,13 @@ def lsfft_gradient(grid: int, res, e, grad_ptr=None):
 
 def lsfft_launch_passes(grid: int, kind: int, count: int) -> None:
     _check(load_library().lsfft_launch_passes(C.c_void_p(grid), int(kind), int(count)))
+
+
+def lsfft_fma_peak(paired: bool = False, reps: int = 3) -> float:
+    """FP32 FMA throughput of the current device in TFLOP/s (benchmark ceiling)."""
+    out = C.c_double()
+    _check(load_library().lsfft_fma_peak(int(bool(paired)), int(reps), C.byref(out)))
+    return out.value
 
 
 # --- convenience wrappers ----------------------------------------------------

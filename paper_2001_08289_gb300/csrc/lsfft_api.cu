@@ -1240,6 +1240,16 @@ int lsfft_launch_passes(lsfft_grid* g, int kind, int count) {
     return LSFFT_OK;
 }
 
+int lsfft_fma_peak(int paired, int reps, double* tflops) {
+    if (!tflops || reps < 1) {
+        g_last_error = "lsfft_fma_peak: null output or reps < 1";
+        return LSFFT_EINVAL;
+    }
+    const cudaError_t e = measure_fma_peak(paired ? 1 : 0, reps, tflops);
+    if (e != cudaSuccess) return fail_cuda(e, "lsfft_fma_peak");
+    return LSFFT_OK;
+}
+
 void lsfft_free_result(lsfft_result* res) {
     if (!res) return;
     big_free(res->E_device);

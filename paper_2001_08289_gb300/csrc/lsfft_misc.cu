@@ -327,3 +327,78 @@ template cudaError_t launch_convert_field<float>(cx<float>*, const double2*, int
 template cudaError_t launch_convert_field<double>(cx<double>*, const double2*, int64_t, int, cudaStream_t);
 
 }  // namespace lsfft
+
+// ---------------------------------------------------------------------------
+// FP32 FMA throughput probe (the arithmetic ceiling reported beside the passes'
+// HBM fractions).  Eight independent chains per thread keep every FMA pipe busy
+// past its latency; the result is stored only if it equals an impossible value,
+// so the chains are not removed.
+// ---------------------------------------------------------------------------
+namespace lsfft {
+
+constexpr int FMA_THREADS = 256, FMA_ITERS = 4096;
+
+template <bool PAIRED>
+__global__ void __launch_bounds__(FMA_THREADS) fma_peak_kernel(float* __restrict__ sink, float a, float b) {
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (float)(threadIdx.x + i);
+    if constexpr (PAIRED) {
+        unsigned long long y[4], av, bv;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(av) : "f"(a));
+        asm("mov.b64 %0, {%1, %1};" : "=l"(bv) : "f"(b));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) asm("mov.b64 %0, {%1, %2};" : "=l"(y[i]) : "f"(x[2 * i]), "f"(x[2 * i + 1]));
+        for (int k = 0; k < FMA_ITERS; ++k) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(y[i]) : "l"(av), "l"(bv));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) asm("mov.b64 {%0, %1}, %2;" : "=f"(x[2 * i]), "=f"(x[2 * i + 1]) : "l"(y[i]));
+    } else {
+        for (int k = 0; k < FMA_ITERS; ++k) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == -1.2345e30f) sink[blockIdx.x] = s;
+}
+
+cudaError_t measure_fma_peak(int paired, int reps, double* tflops) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = sms * 8;
+    float* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaMalloc(&sink, sizeof(float) * blocks);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 0.0;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, 0);
+        if (paired) fma_peak_kernel<true><<<blocks, FMA_THREADS>>>(sink, 0.999f, 1e-3f);
+        else fma_peak_kernel<false><<<blocks, FMA_THREADS>>>(sink, 0.999f, 1e-3f);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0 && ms > 0.f) {   // launch 0 warms up
+            const double flops = 2.0 * 8.0 * FMA_ITERS * (double)blocks * FMA_THREADS;
+            const double tf = flops / (ms * 1e-3) / 1e12;
+            if (tf > best) best = tf;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    *tflops = best;
+    return e;
+}
+
+}  // namespace lsfft

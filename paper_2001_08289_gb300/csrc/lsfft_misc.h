@@ -28,6 +28,7 @@ template <typename T>
 cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, const SchemeParams& prm, int64_t Ntot,
                         int d, int packed, const cx<T>* sigma, int sm_count, cudaStream_t s);
 
+cudaError_t measure_fma_peak(int paired, int reps, double* tflops);
 cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
                             double* hist, int final_mode, cudaStream_t s);
 

@@ -97,3 +97,12 @@ def test_effective_tensor_rejects_null_arguments_without_gpu(lib):
                                            ctypes.c_void_p]
     out = ctypes.create_string_buffer(16 * 9)
     assert lib.lsfft_effective_tensor(None, (ctypes.c_double * 2)(1.0, 0.0), None, out, None) == 1
+
+
+def test_fma_peak_rejects_bad_arguments_without_gpu(lib):
+    import paper_2001_08289_gb300 as L
+
+    L.load_library()
+    out = ctypes.c_double()
+    assert L.load_library().lsfft_fma_peak(0, 0, ctypes.byref(out)) == L.EINVAL
+    assert L.load_library().lsfft_fma_peak(0, 3, None) == L.EINVAL
