@@ -60,11 +60,10 @@ finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const 
     __shared__ double red[FIN_WARPS][NVMAX];
     pdl_wait();
     pdl_trigger();
-    if (!final_mode && ctrl->done) {
-        if (threadIdx.x == 0) ctrl->skipB = 1;
-        return;
-    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // the partials are read before the control block, so that both round trips
+    // to memory overlap (reading them is harmless when the solve is done)
+    const int done = final_mode ? 0 : ctrl->done;
     double x[NVMAX];
 #pragma unroll
     for (int v = 0; v < NVMAX; ++v) x[v] = 0.0;
@@ -74,8 +73,18 @@ finalize_kernel(const double* __restrict__ partials, int nblocks, int nv, const 
         for (int v = 0; v < NVMAX; ++v)
             if (v < nv) x[v] += pb[v];
     }
+    if (done) {
+        if (threadIdx.x == 0) ctrl->skipB = 1;
+        return;
+    }
     int idx;
     const double s = warp_sum_scatter<NVMAX>(x, idx);   // lane pairs share an index
+    if (nw == 1) {   // one warp (row passes of at most 64 blocks): its sums are the totals
+        if ((lane & 1) == 0) tot[idx] = s;
+        __syncwarp();
+        if (lane == 0) finalize_update(tot, P, ctrl, hist, final_mode);
+        return;
+    }
     if ((lane & 1) == 0) red[warp][idx] = s;
     __syncthreads();
     if (warp == 0) {
