@@ -44,6 +44,29 @@ def test_parity_2048_square_array(L, prec, s1, scheme):
     assert np.linalg.norm(E - ref.E) / np.linalg.norm(ref.E) < et
 
 
+@pytest.mark.parametrize("scheme", ["ms", "em_sub"])
+def test_parity_8192_square_array_full_field(L, scheme):
+    """Three updates on the 8192 x 8192 square array in the benchmark's launch
+    configuration (FP32 packed fields, cluster strided pass), element by element
+    against the FP64 oracle run at the same size: sigma_k at every iterate and the
+    whole field in relative L2."""
+    n, iters = 8192, 3
+    mask = square_array_mask(n)
+    e = np.array([1.0, 0.0])
+    with L.Grid(mask) as g:
+        r = g.solve(10.0, e, scheme=scheme, precision="fp32", tol=0.0, max_iter=iters, alpha=0.25, beta=4.0)
+        assert r.packed == 1
+        E = r.field_numpy()
+        hist = r.hist_sigma
+        r.free()
+    ref = S.solve(S.Problem(mask, 10.0, e, "trig"), scheme, alpha=0.25, beta=4.0, tol=0.0, max_iter=iters)
+    st, et = TOL["fp32"]
+    assert np.max(np.abs(hist - ref.hist_sigma) / np.abs(ref.hist_sigma)) < st
+    num = sum(np.linalg.norm((E[c] - ref.E[c]).ravel()) ** 2 for c in range(2))
+    den = sum(np.linalg.norm(ref.E[c].ravel()) ** 2 for c in range(2))
+    assert np.sqrt(num / den) < et
+
+
 def test_8192_first_update_sampled_and_invariants(L):
     """One MS update from E = e on the 8192^2 square array (FP32, the benchmark's
     layout): <E> = e exactly, sigma_1 of the first iterate and E at sampled voxels
