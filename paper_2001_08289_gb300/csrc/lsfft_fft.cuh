@@ -195,26 +195,25 @@ struct LineFFT {
                                                    int tws) {
         // a[r] *= W_span^{jm r}, forward W = exp(-2 pi i / span)
         if constexpr (sizeof(T) == 4) {
-            // W^(jm r) from the bases W^(jm), W^(2 jm), W^(4 jm), W^(8 jm): each power is a
-            // product of at most four bases (a few ulp), formed when needed so that no
-            // table of R twiddles stays live in registers.
+            // W^(jm r), r = lo + 4 hi (lo, hi < 4), as W^(jm lo) W^(4 jm hi): the
+            // powers 1..3 and 4, 8, 12 of W^(jm) from one sincospif and five
+            // products, then one product for each r with lo, hi both nonzero
+            // (14 complex products for R = 16).  Each power is formed when needed,
+            // so no table of R twiddles stays live in registers.
             float s, c;
             sincospif(2.0f * (float)jm / (float)span, &s, &c);
-            C b[4];
-            b[0] = mkc(c, INV ? s : -s);
-#pragma unroll
-            for (int i = 1; i < 4; ++i) b[i] = cmul(b[i - 1], b[i - 1]);
+            C p[4], h[4];
+            p[0] = h[0] = mkc(1.0f, 0.0f);
+            p[1] = mkc(c, INV ? s : -s);
+            if constexpr (R > 2) p[2] = cmul(p[1], p[1]);
+            if constexpr (R > 3) p[3] = cmul(p[2], p[1]);
+            if constexpr (R > 4) h[1] = cmul(p[2], p[2]);
+            if constexpr (R > 8) h[2] = cmul(h[1], h[1]);
+            if constexpr (R > 12) h[3] = cmul(h[2], h[1]);
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = mkc(1.0f, 0.0f);
-                bool first = true;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (r & (1 << i)) {
-                        w = first ? b[i] : cmul(w, b[i]);
-                        first = false;
-                    }
-                }
+                const int lo = r & 3, hi = r >> 2;
+                const C w = lo == 0 ? h[hi] : hi == 0 ? p[lo] : cmul(h[hi], p[lo]);
                 a[r] = cmul(a[r], w);
             }
         } else {
