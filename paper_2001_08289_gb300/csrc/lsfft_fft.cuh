@@ -182,6 +182,17 @@ __device__ __forceinline__ void line_sync() {
     else asm volatile("bar.sync 1, %0;" ::"n"(SYNC) : "memory");
 }
 
+// Number of stages of an n-point line transform with radices <= rmax that
+// exchange through shared memory (all but the last).
+__host__ __device__ constexpr int line_exchanges(int n, int rmax) {
+    int ns = 1, k = 0;
+    while (ns * (n / ns >= rmax ? rmax : n / ns) < n) {
+        ns *= (n / ns >= rmax ? rmax : n / ns);
+        ++k;
+    }
+    return k;
+}
+
 // SMS: element stride of the exchange line in shared memory (SMS lines
 // interleaved position by position share one buffer).
 template <typename T, int N, int E, int RMAX, bool INV, bool PAIRED = false, int SYNC = 0, int SMS = 1>
@@ -233,15 +244,20 @@ struct LineFFT {
     static constexpr bool PRE = sizeof(T) == 8 && E == 2 && RMAX == 2;
     static constexpr int LOGN = ilog2c(N);
 
-    template <int NS>
+    static constexpr int NEX = line_exchanges(N, RMAX);
+
+    // DB: the stages alternate between two exchange buffers (sm, then sm2, ...), so
+    // that a stage writes a buffer whose last readers have already passed the
+    // previous stage's barrier: one barrier per stage instead of two.
+    template <int NS, bool DB = false>
     __device__ __forceinline__ static void stage(C (&v)[E], C* __restrict__ sm, int t, const C* __restrict__ tw,
-                                                 int tws, const C* pre) {
+                                                 int tws, const C* pre, C* __restrict__ sm2 = nullptr) {
         constexpr int REM = N / NS;
         constexpr int R = REM >= RMAX ? RMAX : REM;
         constexpr bool LAST = (NS * R == N);
         constexpr int B = E / R;
         static_assert(E % R == 0, "radix must divide E");
-        if constexpr (!LAST) line_sync<SYNC>();   // previous readers of sm are done
+        if constexpr (!LAST && !DB) line_sync<SYNC>();   // previous readers of sm are done
         // A last stage with several butterflies per thread (R < E): butterfly i has
         // j = t + TL i < NS, so its twiddles W_N^((t + TL i) r) = W_N^(t r) W_E^(i r)
         // share the powers of W_N^t and differ by exact 16th roots of unity
@@ -284,7 +300,8 @@ struct LineFFT {
             line_sync<SYNC>();
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = sm[pad16(t + TL * m) * SMS];
-            stage<NS * R>(v, sm, t, tw, tws, pre);
+            if constexpr (DB) stage<NS * R, true>(v, sm2, t, tw, tws, pre, sm);
+            else stage<NS * R>(v, sm, t, tw, tws, pre);
         }
     }
 
@@ -302,6 +319,15 @@ struct LineFFT {
             for (int s = 1; s < LOGN; ++s) pre[s] = tw[(int64_t)(N >> (s + 1)) * (t & ((1 << s) - 1)) * tws];
         }
         stage<1>(v, sm, t, tw, tws, pre);
+    }
+
+    // The same transform with the exchanges alternating between sm (first) and
+    // sm2.  No barrier precedes the first write into sm: the caller guarantees
+    // that no thread of the line group still reads it.
+    __device__ __forceinline__ static void run2(C (&v)[E], C* __restrict__ sm, C* __restrict__ sm2, int t,
+                                                const C* __restrict__ tw, int tws = 1) {
+        static_assert(!PRE, "two-point FP64 lines keep the single-buffer form");
+        stage<1, true>(v, sm, t, tw, tws, nullptr, sm2);
     }
 };
 

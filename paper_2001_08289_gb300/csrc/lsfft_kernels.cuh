@@ -93,7 +93,12 @@ struct RowCfg {
     static constexpr int LPB = sizeof(T) == 8 && D == 2 ? 1 : cmax(1, (D == 3 ? 64 : 128) / TL);
     static constexpr int THREADS = LPB * TL;
     using P = Pitch<T, N, TL>;
-    static constexpr int S_BYTES = D * LPB * P::S * CS;
+    // packed layout: two staged half rows of pitch HPS; for FP32 lines of >= 2048
+    // points a second exchange line follows them (DBX), so that the packed path's
+    // transforms alternate between two exchange lines (one barrier per stage)
+    static constexpr int HPS = (int)(N / 2 + 4);
+    static constexpr bool DBX = sizeof(T) == 4 && D == 2 && N >= 2048;
+    static constexpr int S_BYTES = cmax(D * LPB * P::S * CS, DBX ? (2 * LPB * HPS + LPB * P::X) * CS : 0);
     static constexpr int X_BYTES = LPB * P::X * CS;
     static constexpr int M_BYTES = roundup16(LPB * N);
     static constexpr int SMEM = S_BYTES + X_BYTES + M_BYTES;
@@ -458,8 +463,10 @@ __global__ void __launch_bounds__(RowCfg<T, N, D>::THREADS, RowCfg<T, N, D>::MIN
 row_pass(const PassArgs<T> A) {
     using Cfg = RowCfg<T, N, D>;
     using C = cx<T>;
+    using InvFFT = LineFFT<T, N, Cfg::E, Cfg::RMAX, true, Cfg::PAIRED>;
+    using FwdFFT = LineFFT<T, N, Cfg::E, Cfg::RMAX, false, Cfg::PAIRED>;
     constexpr int E = Cfg::E, TL = Cfg::TL, LPB = Cfg::LPB, NV = 4 * D + 1;
-    constexpr int PS = Cfg::P::S, PX = Cfg::P::X;
+    constexpr int PS = Cfg::P::S, PX = Cfg::P::X, HPS = Cfg::HPS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
     pdl_trigger();
@@ -474,6 +481,8 @@ row_pass(const PassArgs<T> A) {
     C* Sb = reinterpret_cast<C*>(smem_raw);                                    // [L][LPB][PS]
     const int g = threadIdx.x / TL, t = threadIdx.x % TL;
     C* Xb = reinterpret_cast<C*>(smem_raw + Cfg::S_BYTES) + g * PX;            // exchange line
+    // packed path: the second exchange line, after the two staged half rows
+    C* Xb2 = Sb + 2 * LPB * HPS + g * PX;
     uint8_t* Mb = smem_raw + Cfg::S_BYTES + Cfg::X_BYTES;                      // [LPB][N]
     const int64_t n_items = (A.n_lines + LPB - 1) / LPB;
     // staged lines per row: the d component planes, or in the packed layout the
@@ -484,21 +493,21 @@ row_pass(const PassArgs<T> A) {
 
     // Stage line l of the rows of `item` (and the mask with line 0): one commit group.
     // (chunk counts are compile-time constants in both branches: no runtime division)
-    auto stage_rows = [&](int64_t item, int l, const C* src0, auto chunks, int64_t pitch) {
+    auto stage_rows = [&](int64_t item, int l, const C* src0, auto chunks, int64_t pitch, int dpitch) {
         constexpr int CHL = decltype(chunks)::value;
         for (int i = threadIdx.x; i < LPB * CHL; i += Cfg::THREADS) {
             const int ch = i % CHL, r = i / CHL;
             const int64_t row = item * LPB + r;
             if (row < A.n_lines)
-                cp_async16(reinterpret_cast<unsigned char*>(Sb + (l * LPB + r) * PS) + 16 * ch,
+                cp_async16(reinterpret_cast<unsigned char*>(Sb + (l * LPB + r) * dpitch) + 16 * ch,
                            reinterpret_cast<const unsigned char*>(src0 + row * pitch) + 16 * ch);
         }
     };
     auto prefetch_line = [&](int64_t item, int l) {
         if (A.packed) {
-            if (stage_x) stage_rows(item, l, A.X + l * A.Nh, IntTag<HP * (int)sizeof(C) / 16>{}, HP);
+            if (stage_x) stage_rows(item, l, A.X + l * A.Nh, IntTag<HP * (int)sizeof(C) / 16>{}, HP, HPS);
         } else {
-            stage_rows(item, l, A.X + l * A.Ntot, IntTag<N * (int)sizeof(C) / 16>{}, N);
+            stage_rows(item, l, A.X + l * A.Ntot, IntTag<N * (int)sizeof(C) / 16>{}, N, PS);
         }
         if (l == 0) {
             constexpr int MCH = N / 16;
@@ -569,8 +578,8 @@ row_pass(const PassArgs<T> A) {
             }
             __syncthreads();
         } else {
-            const C* Hx = Sb + g * PS;
-            const C* Hy = Sb + (LPB + g) * PS;
+            const C* Hx = Sb + g * HPS;
+            const C* Hy = Sb + (LPB + g) * HPS;
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int k = t + TL * m;
@@ -582,7 +591,10 @@ row_pass(const PassArgs<T> A) {
                     v[m] = mkc(x.x + y.y, y.x - x.y);
                 }
             }
-            LineFFT<T, N, E, Cfg::RMAX, true, Cfg::PAIRED>::run(v, Xb, t, A.tw);
+            // (the previous readers of Xb, the split of the last item, are behind the
+            // barrier at the start of this item)
+            if constexpr (Cfg::DBX) InvFFT::run2(v, Xb, Xb2, t, A.tw);
+            else InvFFT::run(v, Xb, t, A.tw);
             if constexpr (N <= Cfg::RMAX) __syncthreads();   // (a one-stage transform has no barrier)
         }
         // every thread has read the staging buffers: stage the next item
@@ -659,18 +671,34 @@ row_pass(const PassArgs<T> A) {
             kahan_add(4 * D, sE2);
         }
         if (mode == MODE_ROW_OUTPUT) return;
-        LineFFT<T, N, E, Cfg::RMAX, false, Cfg::PAIRED>::run(v, Xb, t, A.tw);
-        __syncthreads();   // the transform's last reads of the exchange line are done
+        // Split of Z into the half spectra: thread t holds Z(t + TL m); the partner
+        // Z(n - k) of k <= n/2 is Z((TL - t) + TL (E - 1 - m)) (t > 0) or Z(TL (E - m))
+        // (t = 0), always among the upper halves m >= E/2 (k = 0 is its own partner),
+        // so only those go through shared memory.
+        C* Xs;
+        if constexpr (Cfg::DBX) {
+            // two exchange lines: the forward transform starts on the one the inverse
+            // transform did not read last, and the split uses the one the forward
+            // transform did not read last, so neither needs a barrier before it
+            constexpr int NEX = FwdFFT::NEX, INV_LAST = (NEX - 1) % 2, FWD0 = 1 - INV_LAST;
+            constexpr int SPLIT = 1 - (FWD0 + NEX - 1) % 2;
+            FwdFFT::run2(v, FWD0 == 0 ? Xb : Xb2, FWD0 == 0 ? Xb2 : Xb, t, A.tw);
+            Xs = SPLIT == 0 ? Xb : Xb2;
+        } else {
+            FwdFFT::run(v, Xb, t, A.tw);
+            __syncthreads();   // the transform's last reads of the exchange line are done
+            Xs = Xb;
+        }
 #pragma unroll
-        for (int m = 0; m < E; ++m) Xb[pad16(t + TL * m)] = v[m];
+        for (int m = E / 2; m < E; ++m) Xs[pad16(t + TL * m)] = v[m];
         __syncthreads();
         if (active) {
             C* Ho = A.X + row * HP;
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
+            for (int m = 0; m <= E / 2; ++m) {
                 const int k = t + TL * m;
                 if (k <= N / 2) {
-                    const C z = v[m], zp = Xb[pad16((N - k) & (N - 1))];
+                    const C z = v[m], zp = (m == 0 && t == 0) ? v[0] : Xs[pad16((N - k) & (N - 1))];
                     Ho[k] = mkc((T)0.5 * (z.x + zp.x), (T)0.5 * (z.y - zp.y));
                     Ho[A.Nh + k] = mkc((T)0.5 * (z.y + zp.y), (T)0.5 * (zp.x - z.x));
                 }
