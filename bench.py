@@ -414,19 +414,22 @@ def run_ours(args, sigmas):
     cufft["speedup_ours_vs_cufft"] = round(cufft["ms_per_update"] / ours_ms, 2)
 
     # end to end through the C ABI: pinned host mask in, pinned host fields out.
-    # Each solve's field goes to one of two pinned host buffers on a copy stream
-    # (lsfft_copy_field_async) while the next solve runs; a result is freed once
-    # its copy has completed, and every copy has landed before the clock stops.
+    # Each solve's field goes to one of three pinned host buffers on a copy stream
+    # (lsfft_copy_field_async) while the next solves run; up to two copies are in
+    # flight, so a copy slowed down by the passes beside it does not hold up a short
+    # next solve.  A result is freed once its copy has completed, and every copy has
+    # landed before the clock stops.
     e2e = None
     if not args.no_e2e:
+        depth = 2
         mask_pin = torch.from_numpy(mask_np).pin_memory()
-        host_E = [torch.empty((2, n, n), dtype=torch.complex64).pin_memory() for _ in range(2)]
+        host_E = [torch.empty((2, n, n), dtype=torch.complex64).pin_memory() for _ in range(depth + 1)]
         copy_stream = torch.cuda.Stream(device=dev)
         h2d = mask_pin.numel()
         d2h = 0
         e2e_vox = 0
         copies = 0
-        prev = None
+        pending = []   # (result, event recorded after its copy)
         # this box's device-to-host rate into pinned memory, for context (untimed)
         probe = torch.empty((2, n, n), dtype=torch.complex64, device=dev)
         with torch.cuda.stream(copy_stream):
@@ -446,12 +449,16 @@ def run_ours(args, sigmas):
             for s1 in sigmas:
                 for sch in SCHEMES:
                     st, ptr = L.lsfft_solve(h, s1, e, L.make_opts(scheme=sch, **kw))
-                    if prev is not None:
-                        copy_stream.synchronize()
-                        L.lsfft_free_result(prev)
-                    L.lsfft_copy_field_async(ptr, host_E[copies % 2].data_ptr(), False, copy_stream.cuda_stream)
+                    if len(pending) >= depth:
+                        old_ptr, old_ev = pending.pop(0)
+                        old_ev.synchronize()
+                        L.lsfft_free_result(old_ptr)
+                    L.lsfft_copy_field_async(ptr, host_E[copies % (depth + 1)].data_ptr(), False,
+                                             copy_stream.cuda_stream)
+                    ev = torch.cuda.Event()
+                    ev.record(copy_stream)
+                    pending.append((ptr, ev))
                     copies += 1
-                    prev = ptr
                     r = ptr.contents
                     e2e_vox += r.iters * N
                     if _ == 0:
@@ -460,13 +467,13 @@ def run_ours(args, sigmas):
         copy_stream.synchronize()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if prev is not None:
-            L.lsfft_free_result(prev)
+        for old_ptr, _ in pending:
+            L.lsfft_free_result(old_ptr)
         e2e = {"value": e2e_vox / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "d2h_gbps_pinned": round(d2h_gbps, 1),
                "note": "lsfft_create_grid from pinned host mask, lsfft_solve per (sigma1, scheme), "
-                       "lsfft_copy_field_async of every E to pinned host memory on a copy stream (overlapping "
-                       "the next solve), host wall clock until the last copy has landed"}
+                       "lsfft_copy_field_async of every E to pinned host memory on a copy stream (up to two copies "
+                       "in flight, overlapping the next solves), host wall clock until the last copy has landed"}
     grid.close()
 
     if rank != 0:
