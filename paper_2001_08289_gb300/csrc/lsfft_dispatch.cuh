@@ -33,7 +33,8 @@ cudaError_t row_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
             if (e != cudaSuccess) return e;
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, row_pass<T, N, D>, Cfg::THREADS, Cfg::SMEM);
         }
-        return launch_pdl(row_pass<T, N, D>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s, *A);
+        return launch_pdl(row_pass<T, N, D>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
+                          A->pdl, *A);
     }
 }
 
@@ -64,7 +65,7 @@ cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
             return cudaOccupancyMaxActiveClusters(&max_clusters, (const void*)col_pass_cluster<T, N>, &cfg);
         }
         return launch_pdl(col_pass_cluster<T, N>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
-                          *A);
+                          A->pdl, *A);
     } else {
         using Cfg = ColCfg<T, N, D>;
         static int bps = 0;
@@ -89,7 +90,7 @@ cudaError_t col_op(int op, const PassArgs<T>* A, cudaStream_t s, Geom* g) {
                                                                      Cfg::SMEM);
             }
             return launch_pdl(col_pass<T, N, D>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
-                              *A);
+                          A->pdl, *A);
         }
     }
 }

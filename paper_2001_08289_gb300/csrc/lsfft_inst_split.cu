@@ -33,7 +33,7 @@ cudaError_t split_row_sch(int op, const PassArgs<float>* A, cudaStream_t s, Geom
             return e;
         }
         return launch_pdl(row_pass_split<N, SCH>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
-                          *A);
+                          A->pdl, *A);
     }
 }
 
@@ -79,7 +79,8 @@ cudaError_t split_col_op(int op, const PassArgs<float>* A, cudaStream_t s, Geom*
             if (e != cudaSuccess) return e;
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, col_pass_split<M>, Cfg::THREADS, Cfg::SMEM);
         }
-        return launch_pdl(col_pass_split<M>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s, *A);
+        return launch_pdl(col_pass_split<M>, dim3((unsigned)A->grid_blocks), dim3(Cfg::THREADS), Cfg::SMEM, s,
+                          A->pdl, *A);
     }
 }
 

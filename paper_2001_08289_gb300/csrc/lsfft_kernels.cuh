@@ -449,6 +449,7 @@ struct PassArgs {
     int mode;                 // PassMode
     int grid_blocks;          // persistent grid size chosen by the host
     int packed;               // packed real layout (2-D row pass only; the strided pass sees two planes)
+    int pdl;                  // host-side: launch programmatically after the previous kernel (lsfft_pdl.cuh)
     KConst<T> k;
     long long wait_limit;     // bound of every mbarrier wait, in clock cycles
     int extra_tx;             // test hook: bytes announced but never delivered (0 in normal runs)

@@ -115,9 +115,9 @@ cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, cons
 }
 
 cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
-                            double* hist, int final_mode, cudaStream_t s) {
-    return launch_pdl(finalize_kernel, dim3(1), dim3(finalize_threads(nblocks)), 0, s, partials, nblocks, nv, prm,
-                      ctrl, hist, final_mode);
+                            double* hist, int final_mode, int programmatic, cudaStream_t s) {
+    return launch_pdl(finalize_kernel, dim3(1), dim3(finalize_threads(nblocks)), 0, s, programmatic, partials,
+                      nblocks, nv, prm, ctrl, hist, final_mode);
 }
 
 // Small device-to-host transfers (the control block, the history) written by

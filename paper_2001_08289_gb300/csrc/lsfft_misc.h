@@ -30,7 +30,7 @@ cudaError_t launch_init(cx<T>* X, cx<T>* S, cx<T>* Tf, const uint8_t* mask, cons
 
 cudaError_t measure_fma_peak(int paired, int reps, double* tflops);
 cudaError_t launch_finalize(const double* partials, int nblocks, int nv, const SchemeParams& prm, Ctrl* ctrl,
-                            double* hist, int final_mode, cudaStream_t s);
+                            double* hist, int final_mode, int programmatic, cudaStream_t s);
 
 // Copy `bytes` (a multiple of 8) from device memory to the device view of
 // mapped pinned host memory with one small kernel on stream s.
