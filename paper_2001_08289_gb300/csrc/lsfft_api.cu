@@ -582,7 +582,8 @@ PassArgs<T> base_args(lsfft_grid* g, int st) {
     A.mask = g->mask;
     A.sigma = (g->sigma64 && g->sigma_t_prec == (int)(sizeof(T) == 8)) ? (const cx<T>*)g->sigma_t : nullptr;
     A.packed = g->packed;
-    A.pdl = g->d == 2;   // programmatic launches pay off in 2-D only (lsfft_pdl.cuh)
+    A.pdl = 1;                        // programmatic launches, dependents signalled ...
+    A.pdl_early = g->N <= 128 * 128;  // ... at the kernel's start on small grids, else at exit (lsfft_pdl.cuh)
     A.k = make_kconst<T>(*g->prm_host);
     A.ctrl = g->ctrl_dev;
     A.partials = g->partials;
@@ -795,7 +796,7 @@ cudaError_t launch_iteration(lsfft_grid* g, int st, int nblocks, int row_mode) {
     e = cudaEventRecord(g->ev_fork, g->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(g->fin_stream, g->ev_fork, 0);
     if (e == cudaSuccess)
-        e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 0, g->d == 2,
+        e = launch_finalize(g->partials, nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 0, 1,
                             g->fin_stream);
     if (e == cudaSuccess) e = cudaEventRecord(g->ev_join, g->fin_stream);
     if (e != cudaSuccess) return e;
@@ -996,8 +997,8 @@ int poll_solve(lsfft_grid* g) {
         const size_t ebytes = (size_t)g->d * g->N * sizeof(cx<T>);
         CK(big_alloc(&g->cur_E, ebytes, g->stream));
         CK(launch_row<T>(g, g->cur_st, MODE_ROW_OUTPUT, (cx<T>*)g->cur_E));
-        CK(launch_finalize(g->partials, g->cur_nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1,
-                           g->d == 2, g->stream));
+        CK(launch_finalize(g->partials, g->cur_nblocks, 4 * g->d + 1, *g->prm_host, g->ctrl_dev, g->hist, 1, 1,
+                           g->stream));
         CK(cudaEventRecord(g->ev1, g->stream));
         CK(launch_copy_words(g->ctrl_host_dev, g->ctrl_dev, sizeof(Ctrl), g->stream));
         const int L = g->ctrl_host->iter + 1;

@@ -79,7 +79,7 @@ col_pass_cluster(const __grid_constant__ PassArgs<T> A) {
     static_assert(M % BJ == 0, "rows of a block must fill whole TMA boxes");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     pdl_wait();
-    pdl_trigger();
+    if (A.pdl_early) pdl_trigger();
     if (A.ctrl->skipB) return;                         // uniform over the grid: no barrier is reached
 
     cg::cluster_group cluster = cg::this_cluster();

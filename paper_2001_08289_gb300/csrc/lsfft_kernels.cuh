@@ -450,6 +450,7 @@ struct PassArgs {
     int grid_blocks;          // persistent grid size chosen by the host
     int packed;               // packed real layout (2-D row pass only; the strided pass sees two planes)
     int pdl;                  // host-side: launch programmatically after the previous kernel (lsfft_pdl.cuh)
+    int pdl_early;            // signal dependents at the kernel's start (small grids), else at block exit
     KConst<T> k;
     long long wait_limit;     // bound of every mbarrier wait, in clock cycles
     int extra_tx;             // test hook: bytes announced but never delivered (0 in normal runs)
@@ -470,7 +471,7 @@ row_pass(const PassArgs<T> A) {
     constexpr int PS = Cfg::P::S, PX = Cfg::P::X, HPS = Cfg::HPS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();
-    pdl_trigger();
+    if (A.pdl_early) pdl_trigger();
     const int mode = A.mode;
     if (mode != MODE_ROW_OUTPUT && A.ctrl->done) {   // uniform: before any allocation or barrier
         // the solve stopped before this update: its strided passes skip as well
@@ -953,7 +954,7 @@ col_pass(const __grid_constant__ PassArgs<T> A) {
     constexpr int E = Cfg::E, TL = Cfg::TL, COLS = Cfg::COLS, XP = Cfg::XP, EPC = Cfg::EPC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     pdl_wait();
-    pdl_trigger();
+    if (A.pdl_early) pdl_trigger();
     if (A.ctrl->skipB) return;
     const int mode = A.mode;
 

@@ -22,11 +22,16 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // `programmatic` = 0 launches in plain stream order (the kernel's pdl_wait() then
-// returns at once).  The host enables the programmatic form for 2-D grids only:
-// measured per iteration, it saves 7 % at 64^2 (FP64) and 3 % at 512^2 and is
-// neutral at 2048^2 and 8192^2, while 3-D iterations, whose four passes alternate
-// between kernels of different shapes, ran up to 9 % slower with it (256^3:
-// 0.928 vs 0.844 ms; 128^3 and 512^3 1-2 %).
+// returns at once).  Where a kernel signals its dependents matters: signalled at
+// its start (pdl_trigger() right after pdl_wait()), the next pass's blocks are
+// placed while it still runs, which hides launch latency on small grids but slowed
+// iterations whose passes alternate between kernels of different shapes (256^3:
+// 0.928 vs 0.844 ms per iteration with plain launches).  Left to block exit, the
+// dependents are released as the blocks finish; measured per iteration of a
+// 128-iteration EM solve against signalling at the start: 8192^2 1.015 vs 1.030 ms,
+// 512^2 21.5 vs 21.8 us, 256^3 0.837 vs 0.849 ms (plain launches), 128^3 0.106 vs
+// 0.110 ms, but 64^2 (FP64) 18.0 vs 17.6 us.  So the passes signal at their start
+// only on grids of at most 128^2 voxels (PassArgs::pdl_early) and at exit otherwise.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               int programmatic, Args&&... args) {

@@ -141,7 +141,7 @@ row_pass_split(const PassArgs<float> A) {
     using InvFFT = LineFFT<float, N, E, 16, true>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_wait();   // before any access and before the tensor-memory allocation
-    pdl_trigger();
+    if (A.pdl_early) pdl_trigger();
     const int mode = A.mode;
     if (mode != MODE_ROW_OUTPUT && A.ctrl->done) {   // uniform: before any allocation or barrier
         // the solve stopped before this update: its strided passes skip as well
@@ -345,7 +345,7 @@ col_pass_split(const __grid_constant__ PassArgs<float> A) {
     using InvFFT = LineFFT<float, M, E, 16, true, false, COMPUTE, W>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     pdl_wait();
-    pdl_trigger();
+    if (A.pdl_early) pdl_trigger();
     if (A.ctrl->skipB) return;   // uniform over the grid
     // TMA tile destinations need a 128-byte aligned base: the kernel declares no
     // static shared variable, so the dynamic region starts at the window's origin.
