@@ -526,7 +526,7 @@ def _line(metric, value, unit, args, config, **extra):
 
 
 def run_lattice64(args):
-    """Config 1: the 64^2 square array, sigma_1 = 10, FP64, stop at relative change
+    """The 64^2 lattice: the 64^2 square array, sigma_1 = 10, FP64, stop at relative change
     1e-10; MS, EM and both substituted schemes with [alpha, beta] from the oracle's
     dense pole computation on the same grid (weight cutoffs 1e-10 and 1e-3, both
     Green symbols; stored in tests/golden/dense_pole_hulls_64.json by a script that

@@ -1,6 +1,6 @@
 """The stored dense-pole hulls of the 64^2 square array (read by the benchmark's
-config-1 workload) are what the oracle computes, and the exact forward-difference
-hull is the clean interval the survey found."""
+64^2 lattice workload) are what the oracle computes, and the exact forward-difference
+hull is a clean interval, about [0.172, 5.82]."""
 import json
 import os
 
